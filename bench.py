@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of GPU count-sketch Kaczmarz (CSK) on one GB300 per rank.
+
+Workload (one "step" = one whole solve, Algorithm 1 end to end): plain CSK in
+FP32 with FP64 row norms, A 100000 x 500 iid N(0,1), x* iid N(0,1),
+b = A x*, count sketch d = 5000 from a seed, x0 = 0, GEMV residual path,
+stop at RES = ||x - x*||^2 / ||x*||^2 <= 1e-6 (Section 3).  Inputs are seeded
+synthetic Gaussians (the paper's own data are MATLAB randn draws), resident in
+HBM before the timed region; A (200 MB) is larger than the 129 MB L2.
+
+Metric: solves per second (whole job, all ranks); ms_per_step is the
+time-to-RSE<=1e-6 of one solve.  With N ranks each rank solves its own
+independent system (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the plain CPU oracle (the paper's method restated
+in C, FP64) on the same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N_COLS, D, TOL = 100_000, 500, 5000, 1e-6
+WORKLOAD = ("plain CSK FP32 with FP64 row norms: A 100000x500 iid N(0,1), x* iid N(0,1), b=Ax*, "
+            "d=5000 count sketch, x0=0, GEMV residual path, stop at RES<=1e-6")
+METRIC = "solves/s to RES<=1e-6 (plain GPU CSK, A 100000x500 FP32, d=5000)"
+UNIT = "solves/s"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def sketch_bytes(m, n, d, s=4):
+    # read A and b, write+read perm (8 B/row), write At and bt, cnt/off (8 B/bucket)
+    return s * m * n + s * m + 8 * m + s * d * n + s * d + 8 * d
+
+
+def gemv_bytes_per_eval(d, n, s=4):
+    # At (d x n) once per residual evaluation, plus bt, x and the row update
+    return s * d * n + s * (d + 2 * n)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"csk_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _source_hash(*files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_tag: str, src_hash: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(PROFILES, f"{kernel_tag}.traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != src_hash:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_solves(A64, b64, xs, seconds: float, min_solves: int = 1, max_solves: int = 10 ** 9):
+    """Time whole oracle solves of the workload (FP64, all host cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n_done, its = 0, []
+    while n_done < max_solves and (n_done < min_solves or time.perf_counter() - t0 < seconds):
+        r = oracle.csk(A64, b64, D, 0, x_star=xs, tol=TOL, nthreads=cores)
+        its.append(r.iters)
+        n_done += 1
+    dt = time.perf_counter() - t0
+    return n_done, dt, cores, its
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2004_02480_gb300 import synth
+    s = synth.gaussian_system(M, N_COLS, 0, np.float32)
+    A64, b64 = s.A.astype(np.float64), s.b.astype(np.float64)
+    import oracle
+    oracle.build()
+    # warm-up solves, then K timed solves; cap the run at a few minutes
+    t_w = time.perf_counter()
+    for _ in range(max(0, args.warmup)):
+        oracle_solves(A64, b64, s.x_star, 0.0, 1, 1)
+        if time.perf_counter() - t_w > 60:
+            break
+    per = max(time.perf_counter() - t_w, 1e-3) / max(1, args.warmup)
+    k_run = max(1, min(args.steps, int(180.0 / per) if args.warmup else args.steps))
+    n_done, dt, cores, its = oracle_solves(A64, b64, s.x_star, 0.0, k_run, k_run)
+    value = n_done / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "steps_run": n_done, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * dt / n_done, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded N(0,1), paper Section 3 recipe)",
+        "config": {"workload": WORKLOAD, "m": M, "n": N_COLS, "d": D, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_done} whole oracle solves (sketch + literal Algorithm 1, "
+                                   f"mean IT {np.mean(its):.1f}) on {cores} host threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2004_02480_gb300 import csk, synth
+    csk.lib()   # fails loudly when libcsk.so is missing
+
+    s = synth.gaussian_system(M, N_COLS, rank, np.float32)
+    A = torch.from_numpy(s.A).to(dev)
+    b = torch.from_numpy(s.b).to(dev)
+    xs = torch.from_numpy(s.x_star.astype(np.float32)).to(dev)
+    params = csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV)
+    ws = csk._workspace(csk.csk_solve_workspace_size(M, N_COLS, csk.CSK_F32, params), dev)
+    x = torch.empty(N_COLS, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+    infos = torch.empty((K, 64), dtype=torch.uint8, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    pk = [csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV) for _ in range(K)]
+    for i in range(K):
+        csk.set_stage_events(pk[i], ev[i])
+
+    for _ in range(W):
+        csk.csk_solve(A, b, params, x_star=xs, x_out=x, info=infos[0], ws=ws, sync=False)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = csk.csk_kernel_launches()
+    t0.record()
+    for i in range(K):
+        csk.csk_solve(A, b, pk[i], x_star=xs, x_out=x, info=infos[i], ws=ws, sync=False)
+    t1.record()
+    torch.cuda.synchronize()
+    launches = csk.csk_kernel_launches() - l0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+
+    recs = [csk.read_info(infos[i]) for i in range(K)]
+    ok = all(r["status"] == 0 and r["rse"] <= TOL for r in recs)
+    iters = [r["iters"] for r in recs]
+    st_sketch = [ev[i][0].elapsed_time(ev[i][1]) for i in range(K)]
+    st_iter = [ev[i][2].elapsed_time(ev[i][3]) for i in range(K)]
+    st_check = [ev[i][3].elapsed_time(ev[i][4]) for i in range(K)]
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    Ah = torch.from_numpy(s.A).pin_memory().numpy()
+    bh = torch.from_numpy(s.b).pin_memory().numpy()
+    xsh = torch.from_numpy(s.x_star.astype(np.float32)).pin_memory().numpy()
+    xo = torch.empty(N_COLS, dtype=torch.float32).pin_memory().numpy()
+    wsh = csk._workspace(csk.csk_solve_host_workspace_size(M, N_COLS, csk.CSK_F32, params), dev)
+    E = max(1, args.e2e_steps)
+    csk.csk_solve_host(Ah, bh, params, x_star=xsh, ws=wsh, x_out=xo)
+    if world > 1:
+        dist.barrier()
+    te = time.perf_counter()
+    e2e_ok = True
+    for _ in range(E):
+        _, inf, rc = csk.csk_solve_host(Ah, bh, params, x_star=xsh, ws=wsh, x_out=xo)
+        e2e_ok &= rc == 0 and inf["rse"] <= TOL
+    te = time.perf_counter() - te
+
+    if world > 1:
+        t = torch.tensor([ms, te], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, te = float(t[0]), float(t[1])
+        c = torch.tensor([launches, int(ok and e2e_ok)], device=dev, dtype=torch.int64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        launches, ok_ranks = int(c[0]), int(c[1])
+        ok = ok_ranks == world
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = _peaks()
+    mean_it = float(np.mean(iters))
+    it_ms = float(np.mean(st_iter))
+    it_bytes = (mean_it + 1) * gemv_bytes_per_eval(D, N_COLS)
+    achieved = it_bytes / (it_ms * 1e-3) / 1e9
+    sk_ms = float(np.mean(st_sketch))
+    sk_gbs = sketch_bytes(M, N_COLS, D) / (sk_ms * 1e-3) / 1e9
+    src = _source_hash("paper_2004_02480_gb300/csrc/iterate.cu", "paper_2004_02480_gb300/csrc/common.cuh")
+    traffic = _traffic("k_iterate_gemv_100000x500_d5000", src)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n_done, dt, cores, its = oracle_solves(s.A.astype(np.float64), s.b.astype(np.float64),
+                                               s.x_star, args.cpu_seconds)
+        cpu = {"value": n_done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_done} whole oracle solves of this workload (FP64 sketch + literal "
+                         f"Algorithm 1, mean IT {np.mean(its):.1f}) in {dt:.1f} s"}
+
+    value = world * K / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1), paper Section 3 recipe)",
+        "config": {"workload": WORKLOAD, "m": M, "n": N_COLS, "d": D, "tol": TOL, "path": "gemv",
+                   "parallelism": f"replicas x{world} (independent systems)",
+                   "l2": "inputs larger than L2 (A = 200 MB > 129 MB)"},
+        "valid": bool(ok),
+        "breakdown": {"sketch_ms": sk_ms, "iterate_ms": it_ms, "check_ms": float(np.mean(st_check)),
+                      "iters_mean": mean_it, "rse_max": max(r["rse"] for r in recs),
+                      "grid": recs[0]["grid"],
+                      "sketch_gbs": sk_gbs, "sketch_frac_of_" + peak_kind + "_hbm": sk_gbs / hbm},
+        "roofline": {"kernel": "k_iterate_gemv<float>", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": traffic,
+                     "note": "algorithmic bytes = (IT+1) residual evaluations x (4dn + 4(d+2n)); "
+                             "At stays in shared memory, so this is not DRAM traffic"},
+        "e2e": {"value": world * E / te, "unit": UNIT,
+                "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes + 4 * N_COLS),
+                "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * csk.h -- C ABI of the GB300 (sm_103a) Count Sketch Kaczmarz library.
+ *
+ * Method: Zhang & Li, "A Count Sketch Kaczmarz Method For Solving Large
+ * Overdetermined Linear Systems" (arXiv 2004.02480).  The problem is the
+ * consistent system A x = b with A m x n, m >> n (Section 1, eq. (1)).
+ * Algorithm 1 takes A, b, the sketch size d and x0 and returns x: it forms
+ * At = S A and bt = S b with the count sketch S = Phi D of Definition 1,
+ * then repeats the maximal-weighted-residual step
+ *     i_k = argmax_j |bt_j - At_j x_k| / ||At_j||,
+ *     x_{k+1} = x_k + (bt_{i_k} - At_{i_k} x_k) / ||At_{i_k}||^2 * At_{i_k}^T
+ * until RES = ||x_k - x*||^2 / ||x*||^2 <= 1e-6 or the step cap (Section 3).
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major.  A has leading dimension lda >= n (elements).
+ *    Indices are 0-based (the paper's [m], [d] are 1-based).
+ *  - Every pointer named *_dev, and every array argument not marked "host",
+ *    is CUDA device memory on the current device, allocated and owned by the
+ *    caller.  The library never allocates or frees memory on these paths; the
+ *    caller passes a workspace of at least the size the matching
+ *    *_workspace_size function returns, 256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work is enqueued on it; the call returns without
+ *    synchronising.  Calls on different streams must use different
+ *    workspaces and outputs.
+ *  - Errors in the arguments are detected on the host and returned at once
+ *    (CSK_EINVAL, CSK_EUNSUPPORTED); nothing is enqueued then.  A CUDA launch
+ *    error is returned as CSK_ECUDA.  The outcome of the iteration (converged,
+ *    cap reached, numerical failure, wait timeout) is written to the csk_info
+ *    record in device memory when the stream reaches it; the return value
+ *    CSK_OK then means "enqueued".
+ *  - Randomness: the sketch of row i is drawn from the SplitMix64 output
+ *    u_i = mix64(seed + (i+1) * 0x9E3779B97F4A7C15) (Steele, Lea & Flood
+ *    2014): bucket h(i) = ((u_i >> 32) * d) >> 32, sign D_ii = -1 if bit 0 of
+ *    u_i is set, else +1.  Same seed, same sketch, on every device.
+ */
+#ifndef CSK_H
+#define CSK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CSK_OK = 0,            /* converged (in csk_info) / enqueued (return)   */
+    CSK_MAXITER = 1,       /* step cap reached before the tolerance         */
+    CSK_EINVAL = -1,       /* invalid argument (sizes, NULL, workspace)     */
+    CSK_ENOMEM = -2,       /* a size overflows the supported index range    */
+    CSK_ETIMEOUT = -3,     /* an inter-CTA wait exceeded its poll limit     */
+    CSK_ENUMERIC = -4,     /* NaN/Inf residual, or At has no non-zero row   */
+    CSK_ECUDA = -5,        /* a CUDA runtime call failed                    */
+    CSK_EUNSUPPORTED = -6  /* valid request this build does not support     */
+} csk_status;
+
+typedef enum { CSK_F32 = 0, CSK_F64 = 1 } csk_dtype;
+
+/* Residual path of the iteration.
+ *  GEMV: r = bt - At x recomputed every step (Algorithm 1 as printed).
+ *  GRAM: r_{k+1} = r_k - alpha_k G[:, i_k] with G = At At^T formed once on
+ *        the tensor cores in split BF16 (hi*hi + hi*lo + lo*hi, FP32
+ *        accumulation), r_{i_k} set to 0 exactly, and an FP64 recomputation
+ *        of r every refresh_every steps.  Equal to GEMV in exact arithmetic.
+ *  AUTO: the library picks (GEMV when the sketch fits on chip). */
+typedef enum { CSK_RESID_GEMV = 0, CSK_RESID_GRAM = 1, CSK_RESID_AUTO = 2 } csk_resid;
+
+typedef struct {
+    int64_t d;              /* sketch rows; 0 = no sketch (MWRK on A, Remark 1) */
+    uint64_t seed;          /* sketch seed (Definition 1)                       */
+    double tol;             /* RES tolerance, default 1e-6 (Section 3)           */
+    int64_t max_iter;       /* step cap, default 20000 (Section 3)               */
+    int32_t refresh_every;  /* GRAM path: FP64 residual refresh period, 0 = off  */
+    int32_t path;           /* csk_resid                                         */
+    int64_t spin_limit;     /* polls per inter-CTA wait before CSK_ETIMEOUT,
+                               0 = default (about a second)                      */
+    int32_t *ik_log;        /* device, nullable: i_k of step k, k < ik_log_len   */
+    int64_t ik_log_len;
+    int32_t grid;           /* CTAs of the persistent kernel, 0 = library choice */
+    int32_t fault_inject;   /* test hook: 1 = CTA 0 never publishes, so every
+                               wait runs out and the solve ends CSK_ETIMEOUT     */
+    void *x_log;            /* device, nullable: x_k (n elements of the dtype) of
+                               step k < x_log_len, row k of an x_log_len x n
+                               array -- the iterate step k selects from          */
+    int64_t x_log_len;
+    void *stage_events[5];  /* optional cudaEvent_t handles (caller-owned), each
+                               recorded on the stream when non-NULL: [0] before
+                               the sketch, [1] after sketch and row norms, [2]
+                               before the iteration (after the Gram matrix),
+                               [3] after the iteration, [4] after the check     */
+} csk_params;
+
+/* Outcome of one solve, written by the device (64 bytes). */
+typedef struct {
+    int32_t status;         /* csk_status of the solve                          */
+    int32_t path;           /* residual path used (csk_resid)                   */
+    int64_t iters;          /* updates performed (IT of Section 3)              */
+    double rse;             /* ||x - x*||^2 / ||x*||^2 in FP64 (NaN without x*) */
+    double resid;           /* ||bt - At x|| / ||bt|| in FP64                    */
+    int32_t rows;           /* rows iterated on (d, or m without sketch)        */
+    int32_t empty_rows;     /* rows of At with zero norm (excluded, no 0/0)     */
+    int32_t grid;           /* CTAs of the persistent kernel                    */
+    int32_t reserved0;
+    double reserved1;
+    double reserved2;
+} csk_info;
+
+/* Defaults of Section 3: tol 1e-6, max_iter 20000, d = 0 (caller sets it),
+ * seed 0, GEMV path, no refresh, default poll limit, no log. */
+void csk_params_default(csk_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *csk_strerror(int status);
+
+/* ABI version of this header (major * 10000 + minor * 100 + patch). */
+int csk_version(void);
+
+/* Number of CUDA kernels this library has enqueued in this process so far
+ * (all devices and threads).  Lets a caller count the library's launches in
+ * a region by differencing two reads. */
+int64_t csk_kernel_launches(void);
+
+/* ----------------------------------------------------------------------
+ * csk_sketch -- Algorithm 1, "Initialize": At = S A and Bt = S B.
+ *
+ * A     m x n (lda >= n), dtype elements.  B m x nrhs (ldb >= nrhs), may be
+ *       NULL when nrhs == 0.
+ * At    out, d x n, leading dimension n.  Row j is the signed sum of the rows
+ *       i with h(i) = j, added in ascending i (fixed order: an FP32 result
+ *       is reproducible bit for bit).  Bt out, d x nrhs (ld nrhs), nullable.
+ * norms2_out  out, nullable: d doubles, ||At_j||^2 accumulated in FP64.
+ * perm_out    out, nullable: m int32, the rows sorted by (h(i), i).
+ * off_out     out, nullable: d+1 int32, bucket j is perm[off[j] .. off[j+1]).
+ * ws          scratch of csk_sketch_workspace_size(m, d) bytes.
+ * Limits: 1 <= m, n, d <= 2^31 - 1; m * max(n, nrhs) elements addressable.
+ * d >= m is accepted (rows of At may then be zero).
+ * -------------------------------------------------------------------- */
+size_t csk_sketch_workspace_size(int64_t m, int64_t d);
+
+int csk_sketch(const void *A, int64_t m, int64_t n, int64_t lda,
+               const void *B, int64_t ldb, int32_t nrhs, int32_t dtype,
+               int64_t d, uint64_t seed,
+               void *At, void *Bt, double *norms2_out,
+               int32_t *perm_out, int32_t *off_out,
+               void *ws, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------------
+ * csk_solve -- Algorithm 1 end to end for one right-hand side.
+ *
+ * A m x n (lda), b m-vector, dtype CSK_F32 or CSK_F64.  FP32 inputs iterate
+ * in FP32 with FP64 row norms, FP64 refresh and FP64 final check; FP64
+ * inputs iterate in FP64.
+ * params  host pointer; params->d == 0 runs MWRK on A itself (Remark 1).
+ * x0      nullable (x0 = 0); x_star nullable.  With x_star the step loop stops
+ *         when RES <= tol (tested before every step, Section 3); without it
+ *         when ||bt - At x||^2 / ||bt||^2 <= tol.
+ * x_out   out, n elements of dtype.
+ * info    out, device csk_info.
+ * ws      scratch of csk_solve_workspace_size(m, n, dtype, params) bytes.
+ * -------------------------------------------------------------------- */
+size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype,
+                                const csk_params *params);
+
+int csk_solve(const void *A, int64_t m, int64_t n, int64_t lda,
+              const void *b, int32_t dtype, const csk_params *params,
+              const void *x0, const void *x_star, void *x_out,
+              csk_info *info, void *ws, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------------
+ * csk_solve_host -- csk_solve with the problem and the results in HOST
+ * memory: A, b, x0, x_star are copied to the device inside the call, x and
+ * the csk_info record are copied back, and the call returns after the
+ * stream has finished (the host buffers are then valid).  Page-locked host
+ * buffers make the copies asynchronous DMA; pageable ones also work.
+ * ws is DEVICE scratch of csk_solve_host_workspace_size(...) bytes: the
+ * device copies of the inputs plus the workspace of csk_solve.
+ * Return value: the csk_status of the solve itself (CSK_OK, CSK_MAXITER, ...)
+ * once it has finished, or an argument / CUDA error.
+ * -------------------------------------------------------------------- */
+size_t csk_solve_host_workspace_size(int64_t m, int64_t n, int32_t dtype,
+                                     const csk_params *params);
+
+int csk_solve_host(const void *A_host, int64_t m, int64_t n, int64_t lda,
+                   const void *b_host, int32_t dtype, const csk_params *params,
+                   const void *x0_host, const void *x_star_host,
+                   void *x_out_host, csk_info *info_host,
+                   void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSK_H */

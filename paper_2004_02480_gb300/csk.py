@@ -1,0 +1,291 @@
+"""Python binding of libcsk (include/csk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks tensor placement, allocates outputs and
+the workspace with PyTorch on the tensors' device, passes raw pointers and the
+current CUDA stream, and raises :class:`CskError` on a non-zero return code.
+There is no fallback: if ``libcsk.so`` is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcsk.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "csk.h")
+
+CSK_OK, CSK_MAXITER = 0, 1
+CSK_EINVAL, CSK_ENOMEM, CSK_ETIMEOUT, CSK_ENUMERIC, CSK_ECUDA, CSK_EUNSUPPORTED = -1, -2, -3, -4, -5, -6
+CSK_F32, CSK_F64 = 0, 1
+GEMV, GRAM, AUTO = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CskError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib().csk_strerror(code).decode()} ({code})")
+
+
+class csk_params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("seed", ctypes.c_uint64), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int64), ("refresh_every", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
+                ("ik_log", ctypes.c_void_p), ("ik_log_len", ctypes.c_int64),
+                ("grid", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
+                ("x_log", ctypes.c_void_p), ("x_log_len", ctypes.c_int64),
+                ("stage_events", ctypes.c_void_p * 5)]
+
+
+INFO_DTYPE = np.dtype([("status", "<i4"), ("path", "<i4"), ("iters", "<i8"), ("rse", "<f8"),
+                       ("resid", "<f8"), ("rows", "<i4"), ("empty_rows", "<i4"), ("grid", "<i4"),
+                       ("reserved0", "<i4"), ("reserved1", "<f8"), ("reserved2", "<f8")])
+assert INFO_DTYPE.itemsize == 64
+
+
+def lib():
+    """Load libcsk.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcsk.so not found at {LIB_PATH}: build it with "
+                               "paper_2004_02480_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, u64, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                ctypes.c_size_t)
+        L.csk_params_default.argtypes = [ctypes.POINTER(csk_params)]
+        L.csk_strerror.argtypes = [ctypes.c_int]
+        L.csk_strerror.restype = ctypes.c_char_p
+        L.csk_version.restype = ctypes.c_int
+        L.csk_sketch_workspace_size.argtypes = [i64, i64]
+        L.csk_sketch_workspace_size.restype = sz
+        L.csk_sketch.argtypes = [P, i64, i64, i64, P, i64, i32, i32, i64, u64, P, P, P, P, P, P,
+                                 sz, P]
+        L.csk_sketch.restype = ctypes.c_int
+        L.csk_solve_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(csk_params)]
+        L.csk_solve_workspace_size.restype = sz
+        L.csk_solve.argtypes = [P, i64, i64, i64, P, i32, ctypes.POINTER(csk_params), P, P, P, P,
+                                P, sz, P]
+        L.csk_solve.restype = ctypes.c_int
+        L.csk_kernel_launches.restype = ctypes.c_int64
+        L.csk_solve_host_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(csk_params)]
+        L.csk_solve_host_workspace_size.restype = sz
+        L.csk_solve_host.argtypes = [P, i64, i64, i64, P, i32, ctypes.POINTER(csk_params), P, P,
+                                     P, P, P, sz, P]
+        L.csk_solve_host.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/csk.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(csk_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return CSK_F32
+    if t.dtype == torch.float64:
+        return CSK_F64
+    raise TypeError(f"unsupported dtype {t.dtype}: float32 or float64")
+
+
+def _check_cuda(*ts):
+    dev = None
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError("tensors on different devices")
+    return dev
+
+
+def _rowmajor(A: torch.Tensor) -> int:
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D row-major tensor (unit column stride)")
+    return A.stride(0)
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _workspace(nbytes: int, dev) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+
+
+def csk_params_default(**kw) -> csk_params:
+    """Section 3 defaults (tol 1e-6, 20000 steps), overridden by keywords."""
+    p = csk_params()
+    lib().csk_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def csk_kernel_launches() -> int:
+    """Kernels the library has enqueued in this process so far."""
+    return int(lib().csk_kernel_launches())
+
+
+def set_stage_events(params: csk_params, events) -> None:
+    """Attach up to five torch.cuda.Event objects (None to skip) as the
+    stage markers of csk_solve.  Each event is recorded once here so that its
+    CUDA handle exists."""
+    for i in range(5):
+        ev = events[i] if i < len(events) else None
+        if ev is None:
+            params.stage_events[i] = None
+            continue
+        ev.record()
+        params.stage_events[i] = ctypes.c_void_p(int(ev.cuda_event))
+
+
+def csk_sketch_workspace_size(m: int, d: int) -> int:
+    return int(lib().csk_sketch_workspace_size(m, d))
+
+
+@dataclass
+class Sketch:
+    At: torch.Tensor
+    bt: torch.Tensor | None
+    norms2: torch.Tensor | None
+    perm: torch.Tensor | None
+    off: torch.Tensor | None
+
+
+def csk_sketch(A: torch.Tensor, d: int, seed: int, b: torch.Tensor | None = None, *,
+               norms: bool = True, perm: bool = False, off: bool = False,
+               ws: torch.Tensor | None = None) -> Sketch:
+    """At = S A and bt = S b (Algorithm 1, Initialize) on A's device."""
+    dev = _check_cuda(A, b, ws)
+    lda = _rowmajor(A)
+    m, n = A.shape
+    dt = _dtype_code(A)
+    nrhs, ldb, B = 0, 0, None
+    if b is not None:
+        if b.dtype != A.dtype:
+            raise TypeError("b must have A's dtype")
+        B = b.reshape(m, -1)
+        if B.stride(1) != 1:
+            raise ValueError("b must be contiguous along right-hand sides")
+        nrhs, ldb = B.shape[1], B.stride(0)
+    At = torch.empty((d, n), dtype=A.dtype, device=dev)
+    bt = torch.empty((d, nrhs), dtype=A.dtype, device=dev) if nrhs else None
+    N2 = torch.empty(d, dtype=torch.float64, device=dev) if norms else None
+    P = torch.empty(m, dtype=torch.int32, device=dev) if perm else None
+    O = torch.empty(d + 1, dtype=torch.int32, device=dev) if off else None
+    need = csk_sketch_workspace_size(m, d)
+    if ws is None:
+        ws = _workspace(need, dev)
+    rc = lib().csk_sketch(_ptr(A), m, n, lda, _ptr(B), ldb, nrhs, dt, d, seed & (2**64 - 1),
+                          _ptr(At), _ptr(bt), _ptr(N2), _ptr(P), _ptr(O), _ptr(ws), ws.numel(),
+                          _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_sketch")
+    if bt is not None and b.dim() == 1:
+        bt = bt[:, 0]
+    return Sketch(At, bt, N2, P, O)
+
+
+def csk_solve_workspace_size(m: int, n: int, dtype: int, params: csk_params) -> int:
+    return int(lib().csk_solve_workspace_size(m, n, dtype, ctypes.byref(params)))
+
+
+def read_info(info: torch.Tensor) -> dict:
+    """Decode a csk_info record (64 bytes of device memory) on the host."""
+    rec = np.frombuffer(info.cpu().numpy().tobytes(), dtype=INFO_DTYPE)[0]
+    return {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}
+
+
+def csk_solve(A: torch.Tensor, b: torch.Tensor, params: csk_params, x0=None, x_star=None, *,
+              x_out: torch.Tensor | None = None, info: torch.Tensor | None = None,
+              ws: torch.Tensor | None = None, sync: bool = True):
+    """Algorithm 1 end to end; returns (x, info dict or the device info tensor)."""
+    dev = _check_cuda(A, b, x0, x_star, x_out, info, ws)
+    lda = _rowmajor(A)
+    m, n = A.shape
+    dt = _dtype_code(A)
+    for t in (b, x0, x_star):
+        if t is not None and (t.dtype != A.dtype or not t.is_contiguous()):
+            raise TypeError("b, x0, x_star must be contiguous with A's dtype")
+    if x_out is None:
+        x_out = torch.empty(n, dtype=A.dtype, device=dev)
+    if info is None:
+        info = torch.empty(64, dtype=torch.uint8, device=dev)
+    need = csk_solve_workspace_size(m, n, dt, params)
+    if need == 0:
+        raise CskError(CSK_EINVAL, "csk_solve_workspace_size")
+    if ws is None:
+        ws = _workspace(need, dev)
+    rc = lib().csk_solve(_ptr(A), m, n, lda, _ptr(b), dt, ctypes.byref(params), _ptr(x0),
+                         _ptr(x_star), _ptr(x_out), _ptr(info), _ptr(ws), ws.numel(),
+                         _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_solve")
+    if not sync:
+        return x_out, info
+    return x_out, read_info(info)
+
+
+def csk_solve_host_workspace_size(m: int, n: int, dtype: int, params: csk_params) -> int:
+    return int(lib().csk_solve_host_workspace_size(m, n, dtype, ctypes.byref(params)))
+
+
+def csk_solve_host(A: np.ndarray, b: np.ndarray, params: csk_params, x0=None, x_star=None, *,
+                   ws: torch.Tensor, x_out: np.ndarray | None = None,
+                   device=None) -> tuple[np.ndarray, dict, int]:
+    """csk_solve with host (numpy, ideally page-locked) inputs and outputs.
+
+    ``ws`` is a device uint8 tensor of csk_solve_host_workspace_size bytes.
+    Returns (x, info dict, status code of the solve).
+    """
+    if A.ndim != 2 or A.strides[1] != A.itemsize:
+        raise ValueError("A must be 2-D row-major")
+    m, n = A.shape
+    dt = CSK_F32 if A.dtype == np.float32 else CSK_F64 if A.dtype == np.float64 else None
+    if dt is None:
+        raise TypeError("A must be float32 or float64")
+    for t in (b, x0, x_star):
+        if t is not None and (t.dtype != A.dtype or not t.flags.c_contiguous):
+            raise TypeError("b, x0, x_star must be contiguous with A's dtype")
+    if x_out is None:
+        x_out = np.empty(n, A.dtype)
+    info = np.zeros(1, INFO_DTYPE)
+    dev = ws.device if device is None else device
+
+    def hp(a):
+        return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+    rc = lib().csk_solve_host(hp(A), m, n, A.strides[0] // A.itemsize, hp(b), dt,
+                              ctypes.byref(params), hp(x0), hp(x_star), hp(x_out), hp(info),
+                              _ptr(ws), ws.numel(), _stream(dev))
+    if rc < 0 and rc != info["status"][0]:
+        raise CskError(rc, "csk_solve_host")
+    rec = info[0]
+    return x_out, {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}, rc

@@ -1,0 +1,337 @@
+// api.cu -- the C ABI of libcsk (include/csk.h): argument checks, workspace
+// layout and the stream-ordered launch sequence of each entry point.
+#include <atomic>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace csk {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+constexpr int kMaxDevices = 64;
+DevInfo g_dev[kMaxDevices];
+std::once_flag g_dev_once[kMaxDevices];
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+__global__ void k_info_init(csk_info* info, int path, int rows, int grid) {
+    info->status = CSK_OK;
+    info->path = path;
+    info->iters = 0;
+    info->rse = (double)NAN;
+    info->resid = (double)NAN;
+    info->rows = rows;
+    info->empty_rows = 0;
+    info->grid = grid;
+    info->reserved0 = 0;
+    info->reserved1 = 0.0;
+    info->reserved2 = 0.0;
+}
+
+// Workspace of csk_solve, in order (each piece 256-byte aligned):
+//   sort scratch | At (d x n) | bt (d) | N2 (rows) | stop norm (8 doubles) |
+//   slots (2 x kMaxSlots) | x gather (n) | final-check partials |
+//   G (d x d, GRAM) | Gram operand scratch (GRAM)
+constexpr int kMaxSlots = 1024;
+
+struct SolveLayout {
+    size_t sort, At, bt, N2, norm, slots, xg, part, G, gscr, total;
+};
+
+void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLayout* L) {
+    const size_t s = dtype == CSK_F64 ? 8 : 4;
+    const int64_t rows = d > 0 ? d : m;
+    size_t o = 0;
+    L->sort = o;  o += d > 0 ? align256(sort_scratch_bytes(m, d)) : 0;
+    L->At = o;    o += d > 0 ? align256((size_t)d * n * s) : 0;
+    L->bt = o;    o += d > 0 ? align256((size_t)d * s) : 0;
+    L->N2 = o;    o += align256((size_t)rows * 8);
+    L->norm = o;  o += 256;
+    L->slots = o; o += align256((size_t)2 * kMaxSlots * sizeof(Slot));
+    L->xg = o;    o += align256((size_t)n * s);
+    L->part = o;  o += align256(final_check_partials((int)rows) * 8);
+    L->G = o;     o += path == CSK_RESID_GRAM ? align256((size_t)rows * gram_ld((int)rows) * 4) : 0;
+    L->gscr = o;  o += path == CSK_RESID_GRAM ? align256(gram_scratch_bytes((int)rows, (int)n)) : 0;
+    L->total = o;
+}
+
+int check_stream_device(cudaStream_t st) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return CSK_ECUDA;
+    if (st == nullptr) return CSK_OK;
+    int sd = -1;
+    if (cudaStreamGetDevice(st, &sd) != cudaSuccess) return CSK_EINVAL;
+    return sd == cur ? CSK_OK : CSK_EINVAL;
+}
+
+int resolve_path(int path, int dtype, int64_t d) {
+    if (path == CSK_RESID_AUTO) return CSK_RESID_GEMV;
+    (void)dtype; (void)d;
+    return path;
+}
+
+int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk_params* params,
+                     const void* ws) {
+    if (m < 1 || n < 1 || lda < n) return CSK_EINVAL;
+    if (dtype != CSK_F32 && dtype != CSK_F64) return CSK_EINVAL;
+    const int64_t d = params->d;
+    if (d < 0 || !(params->tol >= 0.0) || params->max_iter < 0) return CSK_EINVAL;
+    if (params->ik_log_len < 0 || (params->ik_log_len > 0 && !params->ik_log)) return CSK_EINVAL;
+    if (params->x_log_len < 0 || (params->x_log_len > 0 && !params->x_log)) return CSK_EINVAL;
+    if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_AUTO) return CSK_EINVAL;
+    if (params->grid < 0 || params->refresh_every < 0) return CSK_EINVAL;
+    if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    const int path = resolve_path(params->path, dtype, d);
+    if (path == CSK_RESID_GRAM && dtype != CSK_F32) return CSK_EUNSUPPORTED;
+    if (path == CSK_RESID_GRAM && d == 0) return CSK_EUNSUPPORTED;   // an m x m Gram is pointless
+    return CSK_OK;
+}
+
+// Device staging of csk_solve_host: A (m x n packed), b, x0, x*, x, info.
+struct HostStaging {
+    size_t A, b, x0, xs, x, info, total;
+};
+void host_staging(int64_t m, int64_t n, int dtype, HostStaging* H) {
+    const size_t s = dtype == CSK_F64 ? 8 : 4;
+    size_t o = 0;
+    H->A = o;    o += align256((size_t)m * n * s);
+    H->b = o;    o += align256((size_t)m * s);
+    H->x0 = o;   o += align256((size_t)n * s);
+    H->xs = o;   o += align256((size_t)n * s);
+    H->x = o;    o += align256((size_t)n * s);
+    H->info = o; o += 256;
+    H->total = o;
+}
+
+inline void record(const csk_params* p, int i, cudaStream_t st) {
+    if (p->stage_events[i]) cudaEventRecord(static_cast<cudaEvent_t>(p->stage_events[i]), st);
+}
+
+int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* b, int32_t dtype,
+                  const csk_params* params, const void* x0, const void* x_star, void* x_out,
+                  csk_info* info, void* ws, const SolveLayout& L, cudaStream_t st) {
+    const int64_t d = params->d;
+    const int path = resolve_path(params->path, dtype, d);
+    const int rows = (int)(d > 0 ? d : m);
+    IterConfig cfg;
+    int rc = plan_iterate(path, dtype, rows, (int)n, params->grid, &cfg);
+    if (rc != CSK_OK) return rc;
+    if (cfg.grid > kMaxSlots) return CSK_EUNSUPPORTED;
+
+    char* w = static_cast<char*>(ws);
+    const void* At;
+    const void* bt;
+    int64_t ld;
+    double* N2 = reinterpret_cast<double*>(w + L.N2);
+    record(params, 0, st);
+    k_info_init<<<1, 1, 0, st>>>(info, path, rows, cfg.grid);
+    note_launches(1);
+    if (d > 0) {
+        SortScratch s;
+        carve_sort_scratch(w + L.sort, m, d, &s);
+        if (launch_bucket_sort(m, d, params->seed, s, st) != cudaSuccess) return CSK_ECUDA;
+        if (launch_segsum(dtype, A, lda, (int)n, b, 1, 1, s.perm, s.off, (int)d, params->seed,
+                          w + L.At, w + L.bt, N2, st) != cudaSuccess)
+            return CSK_ECUDA;
+        At = w + L.At;
+        bt = w + L.bt;
+        ld = n;
+    } else {
+        if (launch_row_norms(dtype, A, lda, (int)m, (int)n, N2, st) != cudaSuccess) return CSK_ECUDA;
+        At = A;
+        bt = b;
+        ld = lda;
+    }
+    record(params, 1, st);
+    double* stop_norm = reinterpret_cast<double*>(w + L.norm);
+    if (launch_norm2(dtype, x_star ? x_star : bt, x_star ? n : rows, stop_norm, st) != cudaSuccess)
+        return CSK_ECUDA;
+    Slot* slots = reinterpret_cast<Slot*>(w + L.slots);
+    if (cudaMemsetAsync(slots, 0, (size_t)2 * cfg.grid * sizeof(Slot), st) != cudaSuccess)
+        return CSK_ECUDA;
+    float* G = nullptr;
+    if (path == CSK_RESID_GRAM) {
+        G = reinterpret_cast<float*>(w + L.G);
+        if (launch_gram_split_bf16(static_cast<const float*>(At), rows, (int)n, N2, G, gram_ld(rows),
+                                   w + L.gscr, info, st) != cudaSuccess)
+            return CSK_ECUDA;
+    }
+    record(params, 2, st);
+    IterProblem p;
+    p.dtype = dtype;
+    p.At = At; p.ld = ld; p.d = rows; p.n = (int)n;
+    p.bt = bt; p.N2 = N2;
+    p.x0 = x0; p.xstar = x_star; p.x_out = x_out;
+    p.stop_norm = stop_norm;
+    p.slots = slots;
+    p.xg = w + L.xg;
+    p.G = G; p.ldg = gram_ld(rows);
+    p.refresh_every = params->refresh_every;
+    p.ik_log = params->ik_log; p.ik_log_len = params->ik_log_len;
+    p.x_log = params->x_log; p.x_log_len = params->x_log_len;
+    p.tol = params->tol; p.max_iter = params->max_iter;
+    p.spin_limit = params->spin_limit; p.fault_inject = params->fault_inject;
+    p.info = info;
+    if (launch_iterate(path, p, cfg, st) != cudaSuccess) return CSK_ECUDA;
+    record(params, 3, st);
+    if (launch_final_check(dtype, At, ld, rows, (int)n, bt, N2, x_out, x_star,
+                           reinterpret_cast<double*>(w + L.part), info, st) != cudaSuccess)
+        return CSK_ECUDA;
+    record(params, 4, st);
+    return CSK_OK;
+}
+}  // namespace
+
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int dev_info(DevInfo* out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    std::call_once(g_dev_once[dev], [dev] {
+        DevInfo d;
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, dev);
+        g_dev[dev] = d;
+    });
+    *out = g_dev[dev];
+    return out->sms > 0 ? 0 : -1;
+}
+
+}  // namespace csk
+
+using namespace csk;
+
+extern "C" {
+
+void csk_params_default(csk_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tol = 1e-6;
+    p->max_iter = 20000;
+    p->path = CSK_RESID_GEMV;
+}
+
+const char* csk_strerror(int status) {
+    switch (status) {
+        case CSK_OK: return "CSK_OK";
+        case CSK_MAXITER: return "CSK_MAXITER: step cap reached";
+        case CSK_EINVAL: return "CSK_EINVAL: invalid argument";
+        case CSK_ENOMEM: return "CSK_ENOMEM: size out of supported range";
+        case CSK_ETIMEOUT: return "CSK_ETIMEOUT: inter-CTA wait exceeded its poll limit";
+        case CSK_ENUMERIC: return "CSK_ENUMERIC: NaN/Inf residual or no non-zero row";
+        case CSK_ECUDA: return "CSK_ECUDA: CUDA runtime error";
+        case CSK_EUNSUPPORTED: return "CSK_EUNSUPPORTED: not supported by this build";
+        default: return "unknown csk status";
+    }
+}
+
+int csk_version(void) { return 100; }
+
+int64_t csk_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+size_t csk_sketch_workspace_size(int64_t m, int64_t d) {
+    if (m < 1 || d < 1) return 0;
+    return sort_scratch_bytes(m, d);
+}
+
+int csk_sketch(const void* A, int64_t m, int64_t n, int64_t lda, const void* B, int64_t ldb,
+               int32_t nrhs, int32_t dtype, int64_t d, uint64_t seed, void* At, void* Bt,
+               double* norms2_out, int32_t* perm_out, int32_t* off_out, void* ws,
+               size_t ws_bytes, void* stream) {
+    if (!A || !At || !ws) return CSK_EINVAL;
+    if (m < 1 || n < 1 || d < 1 || lda < n || nrhs < 0) return CSK_EINVAL;
+    if (dtype != CSK_F32 && dtype != CSK_F64) return CSK_EINVAL;
+    if (nrhs > 0 && (!B || !Bt || ldb < nrhs)) return CSK_EINVAL;
+    if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    if (ws_bytes < csk_sketch_workspace_size(m, d)) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    SortScratch s;
+    carve_sort_scratch(ws, m, d, &s);
+    if (perm_out) s.perm = perm_out;
+    if (off_out) s.off = off_out;
+    if (launch_bucket_sort(m, d, seed, s, st) != cudaSuccess) return CSK_ECUDA;
+    if (launch_segsum(dtype, A, lda, (int)n, nrhs > 0 ? B : nullptr, ldb, nrhs, s.perm, s.off,
+                      (int)d, seed, At, Bt, norms2_out, st) != cudaSuccess)
+        return CSK_ECUDA;
+    return CSK_OK;
+}
+
+size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_params* params) {
+    if (!params || m < 1 || n < 1 || params->d < 0) return 0;
+    if (dtype != CSK_F32 && dtype != CSK_F64) return 0;
+    SolveLayout L;
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    return L.total;
+}
+
+int csk_solve(const void* A, int64_t m, int64_t n, int64_t lda, const void* b, int32_t dtype,
+              const csk_params* params, const void* x0, const void* x_star, void* x_out,
+              csk_info* info, void* ws, size_t ws_bytes, void* stream) {
+    if (!A || !b || !params || !x_out || !info || !ws) return CSK_EINVAL;
+    int rc = check_solve_args(m, n, lda, dtype, params, ws);
+    if (rc != CSK_OK) return rc;
+    SolveLayout L;
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    if (ws_bytes < L.total) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    return solve_enqueue(A, m, n, lda, b, dtype, params, x0, x_star, x_out, info, ws, L, st);
+}
+
+size_t csk_solve_host_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_params* params) {
+    const size_t inner = csk_solve_workspace_size(m, n, dtype, params);
+    if (inner == 0) return 0;
+    HostStaging H;
+    host_staging(m, n, dtype, &H);
+    return H.total + inner;
+}
+
+int csk_solve_host(const void* A_host, int64_t m, int64_t n, int64_t lda, const void* b_host,
+                   int32_t dtype, const csk_params* params, const void* x0_host,
+                   const void* x_star_host, void* x_out_host, csk_info* info_host, void* ws,
+                   size_t ws_bytes, void* stream) {
+    if (!A_host || !b_host || !params || !x_out_host || !info_host || !ws) return CSK_EINVAL;
+    int rc = check_solve_args(m, n, lda, dtype, params, ws);
+    if (rc != CSK_OK) return rc;
+    HostStaging H;
+    host_staging(m, n, dtype, &H);
+    SolveLayout L;
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    if (ws_bytes < H.total + L.total) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    const size_t s = dtype == CSK_F64 ? 8 : 4;
+    char* w = static_cast<char*>(ws);
+    void* A = w + H.A;
+    void* b = w + H.b;
+    void* x0 = x0_host ? w + H.x0 : nullptr;
+    void* xs = x_star_host ? w + H.xs : nullptr;
+    void* x = w + H.x;
+    csk_info* info = reinterpret_cast<csk_info*>(w + H.info);
+    // A is packed to leading dimension n on the device
+    CSK_CUDA_TRY(cudaMemcpy2DAsync(A, (size_t)n * s, A_host, (size_t)lda * s, (size_t)n * s,
+                                   (size_t)m, cudaMemcpyHostToDevice, st));
+    CSK_CUDA_TRY(cudaMemcpyAsync(b, b_host, (size_t)m * s, cudaMemcpyHostToDevice, st));
+    if (x0) CSK_CUDA_TRY(cudaMemcpyAsync(x0, x0_host, (size_t)n * s, cudaMemcpyHostToDevice, st));
+    if (xs) CSK_CUDA_TRY(cudaMemcpyAsync(xs, x_star_host, (size_t)n * s, cudaMemcpyHostToDevice, st));
+    rc = solve_enqueue(A, m, n, n, b, dtype, params, x0, xs, x, info, w + H.total, L, st);
+    if (rc != CSK_OK) return rc;
+    CSK_CUDA_TRY(cudaMemcpyAsync(x_out_host, x, (size_t)n * s, cudaMemcpyDeviceToHost, st));
+    CSK_CUDA_TRY(cudaMemcpyAsync(info_host, info, sizeof(csk_info), cudaMemcpyDeviceToHost, st));
+    CSK_CUDA_TRY(cudaStreamSynchronize(st));
+    return info_host->status;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// common.cuh -- device helpers shared by the CSK kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "csk.h"
+
+namespace csk {
+
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------- hashing
+// Count sketch randomness (Definition 1): SplitMix64 output number i+1 of the
+// stream seeded with `seed`, used as a counter-based hash of the row index.
+__host__ __device__ __forceinline__ uint64_t row_hash(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// h(i): multiply-shift reduction of the high 32 bits onto [0, d).
+__host__ __device__ __forceinline__ int32_t row_bucket(uint64_t u, uint32_t d) {
+    return (int32_t)(((u >> 32) * (uint64_t)d) >> 32);
+}
+// D_ii = -1 when bit 0 is set.
+__host__ __device__ __forceinline__ bool row_negative(uint64_t u) { return (u & 1ull) != 0; }
+
+// ------------------------------------------------------- memory ordering
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// --------------------------------------------------- argmax candidates
+// Selection key of Algorithm 1 (squared, weighted): key = r_j^2 / ||At_j||^2.
+// Order: larger key wins; equal keys -> smaller row index (first maximiser).
+// NaN keys win over everything so a numerical failure propagates to the
+// decision every CTA takes.
+struct Cand {
+    double key;     // -1 for "no candidate" (zero row / empty range)
+    double alpha;   // step length r_j / ||At_j||^2 of this row
+    int32_t idx;
+};
+
+__device__ __forceinline__ bool cand_better(double ka, int32_t ia, double kb, int32_t ib) {
+    const bool na = ka != ka, nb = kb != kb;
+    if (na != nb) return na;
+    if (na) return ia < ib;
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+__device__ __forceinline__ void warp_argmax(double& key, double& alpha, int32_t& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        double a2 = __shfl_xor_sync(0xffffffffu, alpha, o);
+        int32_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (cand_better(k2, i2, key, idx)) { key = k2; alpha = a2; idx = i2; }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Slot through which a CTA publishes its candidate for one exchange round.
+// `stamp` is written last with release semantics; a reader that observes the
+// stamp of the round it waits for (acquire) also observes the payload.
+struct __align__(32) Slot {
+    double key;
+    double alpha;
+    double stat;      // partial stopping statistic (||x-x*||^2 or ||r||^2)
+    int32_t idx;
+    uint32_t stamp;
+};
+
+// Status written into csk_info by the first CTA that fails.
+__device__ __forceinline__ void set_status_once(csk_info* info, int32_t st) {
+    atomicCAS(reinterpret_cast<int*>(&info->status), 0, st);
+}
+
+}  // namespace csk
+
+#define CSK_CUDA_TRY(expr)                                 \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return CSK_ECUDA;           \
+    } while (0)

@@ -1,0 +1,344 @@
+// gram.cu -- G = At At^T on the sm_103a tensor cores (tcgen05 + TMA + TMEM),
+// in split BF16.
+//
+// The GRAM residual path updates r_{k+1} = r_k - alpha_k G[:, i_k], which
+// follows from the projection of Algorithm 1 (r = bt - At x, so a step along
+// At_{i_k}^T changes r by -alpha At At_{i_k}^T).  G is formed once:
+//   hi = bf16(At), lo = bf16(At - hi)          (k_split_bf16)
+//   G  ~= hi hi^T + hi lo^T + lo hi^T          (k_gram_tc, FP32 accumulation)
+// The dropped lo lo^T term and the rounding of lo leave a relative error of
+// about 2^-16 per product.  Only tiles on or above the diagonal are computed;
+// each off-diagonal tile is also stored transposed, so G is exactly
+// symmetric.  Finally G_jj := fl32(||At_j||^2) from the FP64 row norms
+// (k_gram_diag), which makes the residual update of the chosen row consistent
+// with the FP64 step length.
+//
+// k_gram_tc: one 128 x 128 output tile per CTA, 128 threads, 2 CTAs per SM.
+//   warp 0 / lane 0   TMA producer: 64-wide K chunks of the A-rows and B-rows
+//                     panels into a 3-stage ring (128B swizzle)
+//   warp 1 / lane 0   MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
+//                     M = 128, N = 128, K = 16, accumulator in TMEM
+//   warp 2            TMEM allocator (128 columns)
+//   warps 0-3         epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
+//                     direct and mirrored global stores
+// K loop: 3 segments of ceil(n/64) chunks: (hi, hi), (hi, lo), (lo, hi).
+// Every mbarrier wait is bounded; on expiry the CTA records CSK_ETIMEOUT,
+// drains its own TMA loads (bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace csk {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int STAGES = 3;
+constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+constexpr int B_BYTES = BN * BK * 2;          // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before giving up
+
+inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 128B swizzle,
+// rows of 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)1 << 46;                         // descriptor version
+    d |= (uint64_t)2 << 61;                         // swizzle: 128B
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B, FP32 D,
+// both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4)                 // D format F32
+                            | (1u << 7)               // A format BF16
+                            | (1u << 10)              // B format BF16
+                            | ((uint32_t)(BN >> 3) << 17)
+                            | ((uint32_t)(BM >> 4) << 24);
+
+// ----------------------------------------------------------------- kernels
+__global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_pad, int k_pad,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+    const int64_t total = (int64_t)d_pad * k_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / k_pad), c = (int)(e - (int64_t)r * k_pad);
+        const float a = (r < d && c < n) ? At[(int64_t)r * n + c] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(a);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(a - __bfloat162float(h));   // a - h is exact
+    }
+}
+
+__global__ void __launch_bounds__(128, 2)
+k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+          int d, int kchunks, float* __restrict__ G, int64_t ldg, csk_info* info) {
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bj < bi) return;                            // lower triangle: mirrored by (bj, bi)
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    // 1024-byte alignment for the 128B-swizzled tiles
+    unsigned char* dsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int fail_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&acc_bar), 1);
+        fail_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int nch = 3 * kchunks;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        bool ok = true;
+        for (int c = 0; c < nch && ok; ++c) {
+            const int s = c % STAGES, r = c / STAGES;
+            if (r > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (r - 1) & 1)) { ok = false; break; }
+            const int seg = c / kchunks, kc = c - seg * kchunks;
+            const CUtensorMap* ma = seg == 2 ? &map_lo : &map_hi;
+            const CUtensorMap* mb = seg == 1 ? &map_lo : &map_hi;
+            const uint32_t sa = smem_u32(dsm + s * STAGE_BYTES);
+            const uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, STAGE_BYTES);
+            tma_load_2d(sa, ma, fb, kc * BK, bi * BM);
+            tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN);
+            issued = c + 1;
+        }
+        if (!ok) {
+            atomicExch(&fail_sh, 1);
+            // drain: wait (bounded) for the loads this thread issued
+            for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+                (void)mbar_wait(smem_u32(&full_bar[c % STAGES]), (c / STAGES) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        bool ok = true;
+        for (int c = 0; c < nch; ++c) {
+            const int s = c % STAGES, r = c / STAGES;
+            if (!mbar_wait(smem_u32(&full_bar[s]), r & 1)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(dsm + s * STAGE_BYTES);
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                tc_mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
+                            (c > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(smem_u32(&empty_bar[s]));    // stage free once these MMAs finish
+        }
+        if (ok) tc_commit(smem_u32(&acc_bar));     // accumulator complete
+        else atomicExch(&fail_sh, 1);
+    }
+    __syncwarp();
+
+    // ---- epilogue: every warp reads its 32 TMEM lanes (= tile rows)
+    const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
+    const int good = __syncthreads_and(acc_ok && !fail_sh);   // uniform over the CTA
+    tc_fence_after();
+    const int row = bi * BM + warp * 32 + lane;
+    if (good) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int col0 = bj * BN + c0;
+            if (row < d) {
+                float* dst = G + (int64_t)row * ldg + col0;
+                if (col0 + 32 <= d) {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4)
+                        *reinterpret_cast<float4*>(dst + q) =
+                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                        __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                } else {
+                    for (int q = 0; q < 32 && col0 + q < d; ++q) dst[q] = __uint_as_float(v[q]);
+                }
+            }
+            if (bj != bi) {
+                // mirrored tile: G[col][row] -- consecutive lanes, consecutive addresses
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (col0 + q < d && row < d) G[(int64_t)(col0 + q) * ldg + row] = __uint_as_float(v[q]);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        set_status_once(info, CSK_ETIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+__global__ void k_gram_diag(const double* __restrict__ N2, int d, float* __restrict__ G, int64_t ldg) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+        G[(int64_t)j * ldg + j] = (float)N2[j];
+}
+
+// --------------------------------------------------------------- host side
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, void* base, int rows, int cols) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int64_t gram_ld(int d) { return round_up(d, 32); }
+
+size_t gram_scratch_bytes(int d, int n) {
+    const int64_t dp = round_up(d, BM), kp = round_up(n, BK);
+    return (size_t)(2 * dp * kp * 2 + 1024);
+}
+
+cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* N2, float* G,
+                                   int64_t ldg, void* scratch, csk_info* info, cudaStream_t st) {
+    const int dp = (int)round_up(d, BM), kp = (int)round_up(n, BK);
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(scratch) + 1023) & ~uintptr_t(1023));
+    __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* lo = hi + (size_t)dp * kp;
+    DevInfo di;
+    if (dev_info(&di) != 0) return cudaErrorUnknown;
+    k_split_bf16<<<di.sms * 8, 256, 0, st>>>(At, d, n, dp, kp, hi, lo);
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, hi, dp, kp) || !make_map(&ml, lo, dp, kp)) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nt = dp / BM;
+    k_gram_tc<<<dim3(nt, nt), 128, smem, st>>>(mh, ml, d, kp / BK, G, ldg, info);
+    k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
+    note_launches(3);
+    return cudaGetLastError();
+}
+
+}  // namespace csk

@@ -1,0 +1,97 @@
+// kernels.h -- host-side launchers of the CSK kernels (internal to libcsk).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "csk.h"
+
+namespace csk {
+
+// Device properties cached per device (SM count, shared memory limits).
+struct DevInfo {
+    int sms = 0;
+    int smem_optin = 0;     // max dynamic shared memory per block (bytes)
+    int coop = 0;           // cooperative launch supported
+};
+int dev_info(DevInfo* out);
+
+// Count of kernels enqueued by the library (csk_kernel_launches).
+void note_launches(int k);
+
+// ------------------------------------------------------------- sketch
+// Scratch of the counting sort: cnt[d], off[d+1], perm_tmp[m], perm[m],
+// scan partials.  All int32.
+struct SortScratch {
+    int32_t* cnt;
+    int32_t* off;
+    int32_t* perm_tmp;
+    int32_t* perm;
+    int32_t* part;
+};
+size_t sort_scratch_bytes(int64_t m, int64_t d);
+void carve_sort_scratch(void* base, int64_t m, int64_t d, SortScratch* s);
+
+// Counting sort of rows by bucket (hist -> scan -> scatter -> per-bucket
+// sort).  Leaves off[d+1] and perm[m] sorted by (h(i), i).
+cudaError_t launch_bucket_sort(int64_t m, int64_t d, uint64_t seed, const SortScratch& s,
+                               cudaStream_t st);
+
+// Segmented signed row sum At = S A, Bt = S B (+ FP64 row norms).
+cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int n, const void* B,
+                          int64_t ldb, int nrhs, const int32_t* perm, const int32_t* off,
+                          int d, uint64_t seed, void* At, void* Bt, double* N2,
+                          cudaStream_t st);
+
+// FP64 squared row norms of a (rows x n, ld) matrix (unsketched path).
+cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int n,
+                             double* N2, cudaStream_t st);
+
+// out[0] = sum_i v_i^2 in FP64 (one block, fixed order).
+cudaError_t launch_norm2(int dtype, const void* v, int64_t len, double* out, cudaStream_t st);
+
+// -------------------------------------------------------------- iterate
+struct IterConfig {
+    int grid = 0;           // CTAs
+    int threads = 256;
+    int rows_per_cta = 0;
+    int cache_rows = 0;     // At slice resident in shared memory (GEMV path)
+    size_t smem = 0;        // dynamic shared memory bytes
+};
+
+struct IterProblem {
+    int dtype;
+    const void* At;  int64_t ld;  int d;  int n;
+    const void* bt;  const double* N2;
+    const void* x0;  const void* xstar;  void* x_out;
+    const double* stop_norm;   // ||x*||^2, or ||bt||^2 without x*
+    Slot* slots;               // 2 * grid
+    void* xg;                  // n elements (GRAM path refresh)
+    const float* G;  int64_t ldg;  // GRAM path
+    int refresh_every;
+    int32_t* ik_log;  int64_t ik_log_len;
+    void* x_log;  int64_t x_log_len;
+    double tol;  int64_t max_iter;  int64_t spin_limit;  int fault_inject;
+    csk_info* info;
+};
+
+int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cfg);
+cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st);
+
+// FP64 final check: info->rse, info->resid, info->empty_rows.
+cudaError_t launch_final_check(int dtype, const void* At, int64_t ld, int d, int n,
+                               const void* bt, const double* N2, const void* x,
+                               const void* xstar, double* partials, csk_info* info,
+                               cudaStream_t st);
+size_t final_check_partials(int d);
+
+// ----------------------------------------------------------------- Gram
+// G = At At^T (d x d, FP32) from split BF16 operands on the tensor cores;
+// G_jj set to fl32(N2_j).
+int64_t gram_ld(int d);   // leading dimension of G (multiple of 32)
+size_t gram_scratch_bytes(int d, int n);
+cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* N2, float* G,
+                                   int64_t ldg, void* scratch, csk_info* info, cudaStream_t st);
+
+}  // namespace csk

@@ -1,0 +1,438 @@
+// sketch.cu -- count sketch formation At = S A, bt = S b (Algorithm 1,
+// "Initialize"; S = Phi D of Definition 1) on sm_103a.
+//
+// Pipeline (all integer work bit-exact, FP work in a fixed order):
+//   k_hist        cnt[j] = #{i : h(i) = j}            (warp-aggregated atomics)
+//   k_scan_*      off = exclusive prefix sum of cnt   (off[d] = m)
+//   k_scatter     perm_tmp: rows grouped by bucket (arbitrary order inside)
+//   k_bucket_sort perm: each bucket sorted by row index, i.e. the rows in
+//                 (h(i), i) order -- unique, so independent of atomic order
+//   k_segsum      At_j = sum_{p in bucket j, ascending} D_ii A_i, Bt likewise,
+//                 and ||At_j||^2 in FP64: one warp per bucket, 128-bit loads.
+#include <climits>
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace csk {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 4096 buckets per tile
+constexpr int kSortCap = 1024;                         // per-warp shared buffer (ints)
+constexpr int kSortWarps = 4;
+
+inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------- histogram
+__global__ void k_hist(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict__ cnt) {
+    // warp-uniform trip count: every lane reaches the match below together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < m;
+        const int32_t j = valid ? row_bucket(row_hash(seed, (uint64_t)i), d) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, j);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[j], __popc(peers));
+    }
+}
+
+// ------------------------------------------------------------------ scan
+// Block-wide exclusive scan of kScanTile int32 values starting at `first`.
+__device__ __forceinline__ int block_scan_tile(const int32_t* __restrict__ cnt, int64_t first,
+                                               int64_t d, int carry_in, int32_t* __restrict__ out,
+                                               int* sh_warp) {
+    const int t = threadIdx.x;
+    const int64_t i0 = first + (int64_t)t * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = (i0 + q < d) ? cnt[i0 + q] : 0;
+    int incl[kScanItems];
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) { run += v[q]; incl[q] = run; }
+    // warp inclusive scan of the per-thread totals
+    int w = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, w, o);
+        if ((int)lane_id() >= o) w += y;
+    }
+    const int warp = t >> 5;
+    if (lane_id() == 31) sh_warp[warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+        int s = (int)lane_id() < (kScanThreads / 32) ? sh_warp[lane_id()] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if ((int)lane_id() >= o) s += y;
+        }
+        sh_warp[lane_id()] = s;   // inclusive totals of warps
+    }
+    __syncthreads();
+    const int warp_excl = warp ? sh_warp[warp - 1] : 0;
+    const int base = carry_in + warp_excl + (w - run);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (i0 + q < d) out[i0 + q] = base + incl[q] - v[q];
+    const int total = sh_warp[kScanThreads / 32 - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_partials(const int32_t* __restrict__ cnt, int64_t d, int32_t* __restrict__ part) {
+    __shared__ int sh[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s += (i0 + q < d) ? cnt[i0 + q] : 0;
+    s = warp_sum(s);
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = sh[threadIdx.x];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_tiles(const int32_t* __restrict__ cnt, int64_t d, const int32_t* __restrict__ part,
+             int32_t* __restrict__ off) {
+    __shared__ int sh[32];
+    __shared__ int carry;
+    // carry-in of this tile: sum of the partials of the tiles before it
+    int s = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) s += part[t];
+    s = warp_sum(s);
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = sh[threadIdx.x];
+        v = warp_sum(v);
+        if (threadIdx.x == 0) carry = v;
+    }
+    __syncthreads();
+    const int c = carry;
+    __syncthreads();
+    const int total = block_scan_tile(cnt, (int64_t)blockIdx.x * kScanTile, d, c, off, sh);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) off[d] = c + total;
+}
+
+// --------------------------------------------------------------- scatter
+__global__ void k_scatter(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict__ cnt,
+                          const int32_t* __restrict__ off, int32_t* __restrict__ perm_tmp) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = lane_id();
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool valid = i < m;
+        const int32_t j = valid ? row_bucket(row_hash(seed, (uint64_t)i), d) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, j);
+        const int leader = __ffs(peers) - 1;
+        const int np = __popc(peers);
+        const int rk = __popc(peers & lanemask_lt());
+        int top = 0;
+        if (valid && lane == leader) top = atomicSub(&cnt[j], np);
+        top = __shfl_sync(0xffffffffu, top, leader);
+        // this group owns bucket-relative slots [top - np, top)
+        if (valid) perm_tmp[off[j] + top - np + rk] = (int32_t)i;
+    }
+}
+
+// -------------------------------------------------- per-bucket row sort
+// One warp per bucket.  Rows inside a bucket are distinct, so the sorted
+// order is unique and the result does not depend on the scatter's order.
+__global__ void __launch_bounds__(kSortWarps * 32)
+k_bucket_sort(int64_t m, uint32_t d, uint64_t seed, const int32_t* __restrict__ off,
+              const int32_t* __restrict__ perm_tmp, int32_t* __restrict__ perm) {
+    __shared__ int32_t buf[kSortWarps][kSortCap];
+    const int warp = threadIdx.x >> 5;
+    const int lane = lane_id();
+    const int64_t nwarps = (int64_t)gridDim.x * kSortWarps;
+    for (int64_t j = (int64_t)blockIdx.x * kSortWarps + warp; j < (int64_t)d; j += nwarps) {
+        const int32_t base = off[j];
+        const int32_t s = off[j + 1] - base;
+        if (s <= 0) continue;
+        if (s <= 32) {
+            const int32_t v = lane < s ? perm_tmp[base + lane] : INT_MAX;
+            int rank = 0;
+            for (int q = 0; q < s; ++q) rank += (__shfl_sync(0xffffffffu, v, q) < v);
+            if (lane < s) perm[base + rank] = v;
+        } else if (s <= kSortCap) {
+            int32_t* b = buf[warp];
+            for (int p = lane; p < s; p += 32) b[p] = perm_tmp[base + p];
+            __syncwarp();
+            for (int p = lane; p < s; p += 32) {
+                const int32_t v = b[p];
+                int rank = 0;
+                for (int q = 0; q < s; ++q) rank += (b[q] < v);
+                perm[base + rank] = v;
+            }
+            __syncwarp();
+        } else {
+            // large bucket: regenerate its rows in ascending order by a
+            // stable compaction over all rows (O(m) per large bucket)
+            int32_t written = 0;
+            for (int64_t i0 = 0; i0 < m; i0 += 32) {
+                const int64_t i = i0 + lane;
+                const bool hit = i < m && row_bucket(row_hash(seed, (uint64_t)i), d) == (int32_t)j;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) perm[base + written + __popc(bal & lanemask_lt())] = (int32_t)i;
+                written += __popc(bal);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- segmented row sum
+template <typename T, int V> struct VecOf;
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <> struct VecOf<double, 1> { using type = double; };
+
+template <typename T, int V>
+__device__ __forceinline__ void vload(const T* p, T (&out)[V]) {
+    using VT = typename VecOf<T, V>::type;
+    VT v = __ldg(reinterpret_cast<const VT*>(p));
+    const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int q = 0; q < V; ++q) out[q] = e[q];
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vstore(T* p, const T (&in)[V]) {
+    using VT = typename VecOf<T, V>::type;
+    VT v;
+    T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+    for (int q = 0; q < V; ++q) e[q] = in[q];
+    *reinterpret_cast<VT*>(p) = v;
+}
+
+// Signed sum of the rows perm[p0..p1) of src (ncols columns) into dst, one
+// warp, ascending p per column.  Returns this lane's sum of squares (FP64).
+template <typename T, int V, int CPL, int U>
+__device__ __forceinline__ double seg_rows(const T* __restrict__ src, int64_t ld, int ncols,
+                                           const int32_t* __restrict__ perm, int32_t p0,
+                                           int32_t p1, uint64_t seed, T* __restrict__ dst) {
+    const int lane = lane_id();
+    double sq = 0.0;
+    for (int c0 = 0; c0 < ncols; c0 += 32 * V * CPL) {
+        T acc[CPL][V];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[c][q] = T(0);
+        for (int32_t pb = p0; pb < p1; pb += 32) {
+            const int32_t myrow = (pb + lane < p1) ? perm[pb + lane] : 0;
+            const int myneg = row_negative(row_hash(seed, (uint64_t)myrow)) ? 1 : 0;
+            const int cnt = min(32, p1 - pb);
+            for (int q0 = 0; q0 < cnt; q0 += U) {
+                T vals[U][CPL][V];
+                int neg[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int32_t row = __shfl_sync(0xffffffffu, myrow, (q0 + u) & 31);
+                    neg[u] = __shfl_sync(0xffffffffu, myneg, (q0 + u) & 31);
+                    const bool valid = q0 + u < cnt;
+                    const T* rp = src + (int64_t)row * ld;
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        const int col = c0 + (c * 32 + lane) * V;
+                        if (valid && col < ncols) {
+                            vload<T, V>(rp + col, vals[u][c]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < V; ++q) vals[u][c][q] = T(0);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (q0 + u < cnt) {
+#pragma unroll
+                        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                            for (int q = 0; q < V; ++q)
+                                acc[c][q] = neg[u] ? acc[c][q] - vals[u][c][q]
+                                                   : acc[c][q] + vals[u][c][q];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int col = c0 + (c * 32 + lane) * V;
+            if (col < ncols) {
+                vstore<T, V>(dst + col, acc[c]);
+#pragma unroll
+                for (int q = 0; q < V; ++q) sq += (double)acc[c][q] * (double)acc[c][q];
+            }
+        }
+    }
+    return sq;
+}
+
+template <typename T, int V, int CPL, int U>
+__global__ void __launch_bounds__(256)
+k_segsum(const T* __restrict__ A, int64_t lda, int n, const T* __restrict__ B, int64_t ldb,
+         int nrhs, const int32_t* __restrict__ perm, const int32_t* __restrict__ off, int d,
+         uint64_t seed, T* __restrict__ At, T* __restrict__ Bt, double* __restrict__ N2) {
+    const int warps_per_block = blockDim.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+    for (int64_t j = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5); j < d; j += nwarps) {
+        const int32_t p0 = off[j], p1 = off[j + 1];
+        double sq = seg_rows<T, V, CPL, U>(A, lda, n, perm, p0, p1, seed, At + j * (int64_t)n);
+        sq = warp_sum(sq);
+        if (N2 && lane_id() == 0) N2[j] = sq;
+        if (B && nrhs > 0)
+            (void)seg_rows<T, 1, 2, 2>(B, ldb, nrhs, perm, p0, p1, seed, Bt + j * (int64_t)nrhs);
+    }
+}
+
+// ----------------------------------------------------------- row norms
+template <typename T>
+__global__ void k_row_norms(const T* __restrict__ A, int64_t ld, int rows, int n,
+                            double* __restrict__ N2) {
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < rows;
+         j += nwarps) {
+        double s = 0.0;
+        for (int c = lane_id(); c < n; c += 32) {
+            const double v = (double)A[j * ld + c];
+            s += v * v;
+        }
+        s = warp_sum(s);
+        if (lane_id() == 0) N2[j] = s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_norm2(const T* __restrict__ v, int64_t len, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        const double t = (double)v[i];
+        s += t * t;
+    }
+    s = warp_sum(s);
+    if (lane_id() == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) out[0] = t;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+size_t sort_scratch_bytes(int64_t m, int64_t d) {
+    const int64_t tiles = (d + kScanTile - 1) / kScanTile;
+    return (size_t)(align_up(4 * d, 256) + align_up(4 * (d + 1), 256) + 2 * align_up(4 * m, 256) +
+                    align_up(4 * tiles, 256));
+}
+
+void carve_sort_scratch(void* base, int64_t m, int64_t d, SortScratch* s) {
+    char* p = static_cast<char*>(base);
+    const int64_t tiles = (d + kScanTile - 1) / kScanTile;
+    s->cnt = reinterpret_cast<int32_t*>(p);       p += align_up(4 * d, 256);
+    s->off = reinterpret_cast<int32_t*>(p);       p += align_up(4 * (d + 1), 256);
+    s->perm_tmp = reinterpret_cast<int32_t*>(p);  p += align_up(4 * m, 256);
+    s->perm = reinterpret_cast<int32_t*>(p);      p += align_up(4 * m, 256);
+    s->part = reinterpret_cast<int32_t*>(p);      p += align_up(4 * tiles, 256);
+    (void)p;
+}
+
+cudaError_t launch_bucket_sort(int64_t m, int64_t d, uint64_t seed, const SortScratch& s,
+                               cudaStream_t st) {
+    DevInfo di;
+    if (dev_info(&di) != 0) return cudaErrorUnknown;
+    cudaError_t e = cudaMemsetAsync(s.cnt, 0, (size_t)d * 4, st);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    int64_t blocks = (m + threads - 1) / threads;
+    if (blocks > (int64_t)di.sms * 16) blocks = (int64_t)di.sms * 16;
+    k_hist<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt);
+    const int64_t tiles = (d + kScanTile - 1) / kScanTile;
+    if (tiles > 1) k_scan_partials<<<(int)tiles, kScanThreads, 0, st>>>(s.cnt, d, s.part);
+    k_scan_tiles<<<(int)tiles, kScanThreads, 0, st>>>(s.cnt, d, s.part, s.off);
+    k_scatter<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt, s.off, s.perm_tmp);
+    int64_t sblocks = (d + kSortWarps - 1) / kSortWarps;
+    if (sblocks > (int64_t)di.sms * 16) sblocks = (int64_t)di.sms * 16;
+    k_bucket_sort<<<(int)sblocks, kSortWarps * 32, 0, st>>>(m, (uint32_t)d, seed, s.off,
+                                                            s.perm_tmp, s.perm);
+    note_launches(tiles > 1 ? 5 : 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int n, const void* B,
+                          int64_t ldb, int nrhs, const int32_t* perm, const int32_t* off,
+                          int d, uint64_t seed, void* At, void* Bt, double* N2,
+                          cudaStream_t st) {
+    DevInfo di;
+    if (dev_info(&di) != 0) return cudaErrorUnknown;
+    const int threads = 256;
+    int64_t blocks = ((int64_t)d + 7) / 8;
+    if (blocks > (int64_t)di.sms * 32) blocks = (int64_t)di.sms * 32;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A);
+    if (dtype == CSK_F32) {
+        const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
+        if (vec)
+            k_segsum<float, 4, 4, 2><<<(int)blocks, threads, 0, st>>>(
+                (const float*)A, lda, n, (const float*)B, ldb, nrhs, perm, off, d, seed,
+                (float*)At, (float*)Bt, N2);
+        else
+            k_segsum<float, 1, 8, 2><<<(int)blocks, threads, 0, st>>>(
+                (const float*)A, lda, n, (const float*)B, ldb, nrhs, perm, off, d, seed,
+                (float*)At, (float*)Bt, N2);
+    } else {
+        const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
+        if (vec)
+            k_segsum<double, 2, 4, 2><<<(int)blocks, threads, 0, st>>>(
+                (const double*)A, lda, n, (const double*)B, ldb, nrhs, perm, off, d, seed,
+                (double*)At, (double*)Bt, N2);
+        else
+            k_segsum<double, 1, 8, 2><<<(int)blocks, threads, 0, st>>>(
+                (const double*)A, lda, n, (const double*)B, ldb, nrhs, perm, off, d, seed,
+                (double*)At, (double*)Bt, N2);
+    }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int n, double* N2,
+                             cudaStream_t st) {
+    DevInfo di;
+    if (dev_info(&di) != 0) return cudaErrorUnknown;
+    int64_t blocks = ((int64_t)rows + 7) / 8;
+    if (blocks > (int64_t)di.sms * 32) blocks = (int64_t)di.sms * 32;
+    if (dtype == CSK_F32)
+        k_row_norms<float><<<(int)blocks, 256, 0, st>>>((const float*)A, ld, rows, n, N2);
+    else
+        k_row_norms<double><<<(int)blocks, 256, 0, st>>>((const double*)A, ld, rows, n, N2);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm2(int dtype, const void* v, int64_t len, double* out, cudaStream_t st) {
+    if (dtype == CSK_F32)
+        k_norm2<float><<<1, 1024, 0, st>>>((const float*)v, len, out);
+    else
+        k_norm2<double><<<1, 1024, 0, st>>>((const double*)v, len, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace csk

@@ -1,0 +1,108 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/csk.h declares, and rejects invalid arguments before
+touching the device."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+from paper_2004_02480_gb300 import csk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(csk.LIB_PATH):
+        from paper_2004_02480_gb300 import build
+        build.build()
+    return csk.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = csk.header_functions()
+    assert "csk_solve" in names and "csk_sketch" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", csk.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(L, n)
+
+
+def test_defaults_follow_section3(L):
+    p = csk.csk_params_default()
+    assert p.tol == 1e-6 and p.max_iter == 20000 and p.d == 0 and p.path == csk.GEMV
+    assert L.csk_version() >= 100
+    for code in (0, 1, -1, -2, -3, -4, -5, -6):
+        assert L.csk_strerror(code).startswith(b"CSK_")
+
+
+def test_workspace_sizes(L):
+    assert L.csk_sketch_workspace_size(0, 5) == 0
+    assert L.csk_sketch_workspace_size(10, 0) == 0
+    a = L.csk_sketch_workspace_size(1000, 10)
+    b = L.csk_sketch_workspace_size(100000, 10)
+    assert 0 < a < b and a % 256 == 0
+    p = csk.csk_params_default(d=500)
+    s1 = csk.csk_solve_workspace_size(2000, 50, csk.CSK_F64, p)
+    s2 = csk.csk_solve_workspace_size(2000, 50, csk.CSK_F32, p)
+    assert s1 > s2 > 0
+    p0 = csk.csk_params_default(d=0)
+    assert csk.csk_solve_workspace_size(2000, 50, csk.CSK_F32, p0) > 0
+    assert csk.csk_solve_workspace_size(2000, 50, 7, p) == 0
+
+
+def test_invalid_arguments_rejected_on_host(L):
+    fake = ctypes.c_void_p(256)          # never dereferenced: checks come first
+    V = ctypes.c_void_p
+    # NULL A, m < 1, lda < n, bad dtype, d < 1
+    assert L.csk_sketch(None, 10, 2, 2, None, 0, 0, 0, 3, 0, fake, None, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    assert L.csk_sketch(fake, 0, 2, 2, None, 0, 0, 0, 3, 0, fake, None, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    assert L.csk_sketch(fake, 10, 4, 2, None, 0, 0, 0, 3, 0, fake, None, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    assert L.csk_sketch(fake, 10, 2, 2, None, 0, 0, 5, 3, 0, fake, None, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    assert L.csk_sketch(fake, 10, 2, 2, None, 0, 0, 0, 0, 0, fake, None, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    # workspace too small / misaligned
+    assert L.csk_sketch(fake, 10, 2, 2, None, 0, 0, 0, 3, 0, fake, None, None, None, None,
+                        fake, 16, None) == csk.CSK_EINVAL
+    assert L.csk_sketch(fake, 10, 2, 2, None, 0, 0, 0, 3, 0, fake, None, None, None, None,
+                        V(264), 1 << 20, None) == csk.CSK_EINVAL
+    # nrhs > 0 without B
+    assert L.csk_sketch(fake, 10, 2, 2, None, 0, 1, 0, 3, 0, fake, fake, None, None, None,
+                        fake, 1 << 20, None) == csk.CSK_EINVAL
+    # too large for 32-bit row indices
+    assert L.csk_sketch(fake, 1 << 32, 2, 2, None, 0, 0, 0, 3, 0, fake, None, None, None,
+                        None, fake, 1 << 20, None) == csk.CSK_ENOMEM
+    p = csk.csk_params_default(d=3)
+    bp = ctypes.byref(p)
+    assert L.csk_solve(fake, 10, 2, 2, None, 0, bp, None, None, fake, fake, fake, 1 << 30,
+                       None) == csk.CSK_EINVAL
+    assert L.csk_solve(fake, 10, 2, 2, fake, 0, None, None, None, fake, fake, fake, 1 << 30,
+                       None) == csk.CSK_EINVAL
+    assert L.csk_solve(fake, 10, 2, 2, fake, 0, bp, None, None, fake, fake, fake, 8,
+                       None) == csk.CSK_EINVAL
+    bad = csk.csk_params_default(d=3, tol=-1.0)
+    assert L.csk_solve(fake, 10, 2, 2, fake, 0, ctypes.byref(bad), None, None, fake, fake, fake,
+                       1 << 30, None) == csk.CSK_EINVAL
+    bad = csk.csk_params_default(d=3, ik_log_len=5)
+    assert L.csk_solve(fake, 10, 2, 2, fake, 0, ctypes.byref(bad), None, None, fake, fake, fake,
+                       1 << 30, None) == csk.CSK_EINVAL
+    g = csk.csk_params_default(d=3, path=csk.GRAM)
+    assert L.csk_solve(fake, 10, 2, 2, fake, 1, ctypes.byref(g), None, None, fake, fake, fake,
+                       1 << 30, None) == csk.CSK_EUNSUPPORTED
+    g0 = csk.csk_params_default(d=0, path=csk.GRAM)
+    assert L.csk_solve(fake, 10, 2, 2, fake, 0, ctypes.byref(g0), None, None, fake, fake, fake,
+                       1 << 30, None) == csk.CSK_EUNSUPPORTED
+
+
+def test_binding_refuses_cpu_tensors():
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        csk.csk_sketch(torch.zeros(4, 2), 2, 0)

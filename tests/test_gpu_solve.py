@@ -1,0 +1,212 @@
+"""GPU parity of csk_solve (Algorithm 1 end to end) against the CPU oracle.
+
+* FP64 (the 2000 x 50, d = 500 workload): the GPU iterates in FP64 on a sketch
+  that is bit-identical to the oracle's, so the row sequence i_k must equal
+  the oracle's at every step whose selection gap exceeds 1e-9 (only rounding
+  order differs), and IT must match.
+* FP32 (the 100000 x 500, d = 5000 workload): the oracle iterates in FP64 on
+  the GPU's (bit-exact) FP32 sketch; i_k must match over the first
+  min(1000, k_tau) steps, k_tau being the first step whose relative gap
+  between the two best weighted residuals is below tau = 1e-3 (FP32 residuals
+  carry ~1e-6 relative error at n = 500).
+* Every solve must reach RES <= 1e-6 and the final FP64 check must agree with
+  the oracle's recomputation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_02480_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def csk():
+    from paper_2004_02480_gb300 import build, csk as _csk
+    build.build()
+    return _csk
+
+
+def _to(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _solve(csk, sysm, d, seed, log=0, xlog=0, **kw):
+    A, b, xs = _to(sysm.A), _to(sysm.b), _to(sysm.x_star.astype(sysm.A.dtype))
+    ik = torch.full((max(log, 1),), -1, dtype=torch.int32, device=DEV)
+    n = sysm.A.shape[1]
+    X = torch.zeros((max(xlog, 1), n), dtype=A.dtype, device=DEV)
+    p = csk.csk_params_default(d=d, seed=seed, ik_log=ik.data_ptr() if log else None,
+                               ik_log_len=log, x_log=X.data_ptr() if xlog else None,
+                               x_log_len=xlog, **kw)
+    x, info = csk.csk_solve(A, b, p, x_star=xs)
+    if xlog:
+        return x.cpu().numpy(), info, ik.cpu().numpy()[:log], X.cpu().numpy()
+    return x.cpu().numpy(), info, ik.cpu().numpy()[:log]
+
+
+def _check_steps(At, bt, X, ik, steps, u):
+    """Every GPU step, replayed in FP64 from the GPU's own iterate x_k:
+    (1) i_k is a maximiser of r_j^2 / ||At_j||^2 within the worst-case
+        rounding bound of the kernel's arithmetic (unit roundoff u, a sum of
+        n + 1 terms: |dr_j| <= gamma_{n+1} (|bt_j| + sum_c |At_jc x_c|), plus
+        a few roundings for the key itself), and
+    (2) x_{k+1} - x_k is the projection step alpha At_{i_k} of Algorithm 1 to
+        the same accuracy."""
+    At = At.astype(np.float64)
+    bt = bt.astype(np.float64)
+    d, n = At.shape
+    N = np.sum(At * At, axis=1)
+    g = (n + 1) * u / (1 - (n + 1) * u)
+    absA = np.abs(At)
+    Xd = X[:steps + 1].astype(np.float64)
+    R = bt[:, None] - At @ Xd.T                       # d x (steps+1)
+    B = np.abs(bt)[:, None] + absA @ np.abs(Xd).T
+    valid = N > 0
+    for k in range(steps):
+        r, bnd = R[:, k], g * B[:, k]
+        lo = np.where(valid, np.maximum(np.abs(r) - bnd, 0) ** 2 / np.where(valid, N, 1), -1)
+        hi = np.where(valid, (np.abs(r) + bnd) ** 2 / np.where(valid, N, 1), -1)
+        j = ik[k]
+        assert valid[j], k
+        assert hi[j] * (1 + 8 * u) >= lo.max() * (1 - 8 * u), (k, j, hi[j], lo.max())
+        step = Xd[k + 1] - Xd[k]
+        alpha = r[j] / N[j]
+        da = (bnd[j] / N[j]) + 8 * u * abs(alpha)
+        err = np.abs(step - alpha * At[j])
+        assert np.all(err <= da * absA[j] + 4 * u * (np.abs(Xd[k]) + np.abs(Xd[k + 1]))), k
+    return steps
+
+
+def _compare_prefix(ik_gpu, ref, tau):
+    gap = ref.gap
+    k_tau = int(np.argmax(gap < tau)) if np.any(gap < tau) else len(gap)
+    K = min(1000, k_tau, len(ik_gpu), len(ref.ik))
+    assert np.array_equal(ik_gpu[:K], ref.ik[:K]), (K, np.flatnonzero(ik_gpu[:K] != ref.ik[:K])[:5])
+    return K
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_config1_fp64_matches_oracle(csk, seed):
+    m, n, d = 2000, 50, 500
+    s = synth.gaussian_system(m, n, seed, np.float64)
+    x, info, ik = _solve(csk, s, d, seed, log=2000)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At, bt, x_star=s.x_star, tol=1e-6, log_len=2000)
+    assert info["status"] == 0 and ref.status == 0
+    assert info["rse"] <= 1e-6
+    K = _compare_prefix(ik, ref, 1e-9)
+    if K == ref.iters:
+        assert info["iters"] == ref.iters
+    assert np.sum((x - ref.x) ** 2) / np.sum(s.x_star ** 2) <= 1e-6
+    rse, res = oracle.final_check(At, bt, x, s.x_star)
+    assert abs(info["rse"] - rse) <= 1e-12 * max(rse, 1e-30) + 1e-18
+    assert abs(info["resid"] - res) <= 1e-10 * res + 1e-18
+    assert info["empty_rows"] == int(np.sum(np.sum(At ** 2, axis=1) == 0))
+
+
+@pytest.mark.parametrize("grid", [0, 1, 3, 64])
+def test_grid_shape_does_not_change_result(csk, grid):
+    """Every CTA count gives the same iterates: each row's residual is one
+    warp's dot product whichever CTA owns it, and every CTA reduces the same
+    candidates, so i_k and x do not depend on the grid."""
+    s = synth.gaussian_system(3000, 40, 7, np.float64)
+    x0, i0, _ = _solve(csk, s, 400, 7, grid=1)
+    x1, i1, _ = _solve(csk, s, 400, 7, grid=grid)
+    assert i0["iters"] == i1["iters"]
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-12 * np.abs(x0).max())
+
+
+def test_config2_fp32_gemv_matches_oracle(csk):
+    """100000 x 500 FP32, d = 5000: exact i_k prefix up to the first near-tie
+    (tau = 1e-3), every step valid within FP32 rounding, RES <= 1e-6, IT
+    within 5 % of the FP64 oracle's on the same sketch."""
+    m, n, d, seed = 100000, 500, 5000, 0
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x, info, ik, X = _solve(csk, s, d, seed, log=20000, xlog=20000, path=csk.GEMV)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At32.astype(np.float64), bt32.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+    K = _compare_prefix(ik, ref, 1e-3)
+    assert K >= 1
+    assert _check_steps(At32, bt32, X, ik, info["iters"] - 1, 2.0 ** -24) > 500
+    assert abs(info["iters"] - ref.iters) <= 0.05 * ref.iters
+    assert np.sum((x - ref.x) ** 2) / np.sum(s.x_star ** 2) <= 4e-6
+
+
+def test_unsketched_mwrk_matches_oracle(csk):
+    """Remark 1: d = 0 runs MWRK on A itself."""
+    s = synth.gaussian_system(20000, 100, 3, np.float32)
+    x, info, ik, X = _solve(csk, s, 0, 0, log=5000, xlog=5000)
+    ref = oracle.mwrk(s.A.astype(np.float64), s.b.astype(np.float64), x_star=s.x_star,
+                      log_len=5000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6 and info["rows"] == 20000
+    _compare_prefix(ik, ref, 1e-3)
+    _check_steps(s.A, s.b, X, ik, info["iters"] - 1, 2.0 ** -24)
+    assert abs(info["iters"] - ref.iters) <= max(2, 0.05 * ref.iters)
+
+
+@pytest.mark.parametrize("m,n,d,dt", [(1, 1, 1, np.float64), (5, 1, 3, np.float32),
+                                      (50, 3, 200, np.float64), (3000, 50, 500, np.float32),
+                                      (2001, 33, 257, np.float32), (4096, 1, 1, np.float64)])
+def test_edge_shapes(csk, m, n, d, dt):
+    """Tiny, ragged, d > m (empty rows), n = 1 and d = 1 (a single row)."""
+    s = synth.gaussian_system(m, n, m + n, dt)
+    x, info, _ = _solve(csk, s, d, 1, max_iter=20000)
+    h, sg = oracle.count_sketch_map(1, m, d)
+    At, bt = oracle.sketch(s.A.astype(np.float64), s.b.astype(np.float64), h, sg, d)
+    ref = oracle.mwrk(At, bt, x_star=s.x_star, tol=1e-6, max_iter=20000)
+    assert info["status"] == ref.status
+    if ref.status == 0:
+        assert info["rse"] <= 1e-6
+    assert info["empty_rows"] == int(np.sum(np.sum(At ** 2, axis=1) == 0))
+
+
+def test_max_iter_cap(csk):
+    s = synth.gaussian_system(2000, 50, 4, np.float64)
+    x, info, _ = _solve(csk, s, 500, 4, max_iter=10)
+    assert info["status"] == 1 and info["iters"] == 10
+
+
+def test_nan_input_is_numeric_failure(csk):
+    s = synth.gaussian_system(2000, 50, 5, np.float32)
+    s.A[17, 3] = np.nan
+    x, info, _ = _solve(csk, s, 500, 5)
+    assert info["status"] == -4
+
+
+def test_wait_timeout_returns_status_and_context_survives(csk):
+    """Failure detection without a fault: CTA 0 never publishes, every wait
+    runs out of polls, the kernel returns CSK_ETIMEOUT, and the next solve
+    on the same context works."""
+    s = synth.gaussian_system(3000, 40, 6, np.float32)
+    x, info, _ = _solve(csk, s, 400, 6, grid=4, spin_limit=20000, fault_inject=1)
+    assert info["status"] == -3
+    x, info, _ = _solve(csk, s, 400, 6, grid=4)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+
+
+def test_determinism(csk):
+    s = synth.gaussian_system(100000, 500, 1, np.float32)
+    x1, i1, k1 = _solve(csk, s, 5000, 1, log=5000)
+    x2, i2, k2 = _solve(csk, s, 5000, 1, log=5000)
+    assert i1["iters"] == i2["iters"] and np.array_equal(k1, k2)
+    assert np.array_equal(x1.view(np.uint32), x2.view(np.uint32))
+
+
+def test_no_xstar_residual_stop(csk):
+    """Without x*, the loop stops on ||bt - At x||^2 / ||bt||^2 <= tol."""
+    s = synth.gaussian_system(2000, 50, 8, np.float64)
+    p = csk.csk_params_default(d=500, seed=8, tol=1e-12)
+    x, info = csk.csk_solve(_to(s.A), _to(s.b), p)
+    h, sg = oracle.count_sketch_map(8, 2000, 500)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, 500)
+    ref = oracle.mwrk(At, bt, tol=1e-12)
+    assert info["status"] == 0 and info["resid"] ** 2 <= 1.0001e-12
+    assert abs(info["iters"] - ref.iters) <= 1
