@@ -146,6 +146,27 @@ int csk_sketch(const void *A, int64_t m, int64_t n, int64_t lda,
                void *ws, size_t ws_bytes, void *stream);
 
 /* ----------------------------------------------------------------------
+ * csk_gram -- G = At At^T (d x d, FP32) on the tensor cores, split BF16.
+ *
+ * The residual of Algorithm 1 after the projection onto row i_k changes by
+ * -alpha_k At At_{i_k}^T (from x_{k+1} = x_k + alpha_k At_{i_k}^T), so with G
+ * the per-step residual update costs O(d) instead of O(dn).  G is formed as
+ * hi hi^T + hi lo^T + lo hi^T with hi = bf16(At), lo = bf16(At - hi) (FP32
+ * accumulation; about 2^-16 relative error per product).  Only tiles on or
+ * above the diagonal are computed and mirrored, so G is exactly symmetric.
+ * At     d x n FP32, leading dimension n.
+ * norms2 nullable: d doubles; when given, G_jj is set to fl32(norms2_j).
+ * G      out, d x d with leading dimension ldg >= d (ldg % 4 == 0 is fastest).
+ * info   nullable device csk_info: status CSK_ETIMEOUT if a wait ran out.
+ * ws     scratch of csk_gram_workspace_size(d, n) bytes (the BF16 operands).
+ * -------------------------------------------------------------------- */
+size_t csk_gram_workspace_size(int64_t d, int64_t n);
+
+int csk_gram(const float *At, int64_t d, int64_t n, const double *norms2,
+             float *G, int64_t ldg, csk_info *info, void *ws, size_t ws_bytes,
+             void *stream);
+
+/* ----------------------------------------------------------------------
  * csk_solve -- Algorithm 1 end to end for one right-hand side.
  *
  * A m x n (lda), b m-vector, dtype CSK_F32 or CSK_F64.  FP32 inputs iterate

@@ -81,6 +81,7 @@ def _load():
         lib.or_bf16_round.restype = ctypes.c_float
         lib.or_gram_f64.argtypes = [P, i64, i64, i64, P]
         lib.or_gram_split_bf16.argtypes = [P, i64, i64, i64, P]
+        lib.or_gram_split_bf16_rows.argtypes = [P, i64, i64, i64, P, i64, P]
         _lib = lib
         return lib
 
@@ -252,4 +253,14 @@ def gram_split_bf16(At):
     d, n = At.shape
     G = np.empty((d, d), np.float64)
     _load().or_gram_split_bf16(_p(At), d, n, n, _p(G))
+    return G
+
+
+def gram_split_bf16_rows(At, rows):
+    """Rows ``rows`` of the split-BF16 Gram product (len(rows) x d, binary64)."""
+    At = _c(At, np.float32)
+    d, n = At.shape
+    rows = _c(rows, np.int64)
+    G = np.empty((rows.shape[0], d), np.float64)
+    _load().or_gram_split_bf16_rows(_p(At), d, n, n, _p(rows), rows.shape[0], _p(G))
     return G

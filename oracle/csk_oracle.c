@@ -338,3 +338,31 @@ void or_gram_split_bf16(const float *At, int64_t d, int64_t n, int64_t ld,
         }
     free(hi); free(lo);
 }
+
+void or_gram_split_bf16_rows(const float *At, int64_t d, int64_t n, int64_t ld,
+                             const int64_t *rows, int64_t nrows, double *Grows)
+{
+    double *hi = (double *)malloc((size_t)(d * n) * sizeof(double));
+    double *lo = (double *)malloc((size_t)(d * n) * sizeof(double));
+    for (int64_t i = 0; i < d; ++i)
+        for (int64_t c = 0; c < n; ++c) {
+            float a = At[i * ld + c];
+            float h = or_bf16_round(a);
+            float l = or_bf16_round(a - h);
+            hi[i * n + c] = (double)h;
+            lo[i * n + c] = (double)l;
+        }
+    for (int64_t q = 0; q < nrows; ++q) {
+        int64_t i = rows[q];
+        for (int64_t j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int64_t c = 0; c < n; ++c) {
+                s += hi[i * n + c] * hi[j * n + c];
+                s += hi[i * n + c] * lo[j * n + c];
+                s += lo[i * n + c] * hi[j * n + c];
+            }
+            Grows[q * d + j] = s;
+        }
+    }
+    free(hi); free(lo);
+}

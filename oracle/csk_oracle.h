@@ -123,6 +123,11 @@ void or_gram_f64(const double *At, int64_t d, int64_t n, int64_t ld,
 void or_gram_split_bf16(const float *At, int64_t d, int64_t n, int64_t ld,
                         double *G);
 
+/* Rows rows[0..nrows) of the split-BF16 product above (nrows x d, binary64),
+ * for checks at sizes where the whole d x d matrix is too large. */
+void or_gram_split_bf16_rows(const float *At, int64_t d, int64_t n, int64_t ld,
+                             const int64_t *rows, int64_t nrows, double *Grows);
+
 #ifdef __cplusplus
 }
 #endif

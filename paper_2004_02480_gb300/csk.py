@@ -80,6 +80,10 @@ def lib():
                                 P, sz, P]
         L.csk_solve.restype = ctypes.c_int
         L.csk_kernel_launches.restype = ctypes.c_int64
+        L.csk_gram_workspace_size.argtypes = [i64, i64]
+        L.csk_gram_workspace_size.restype = sz
+        L.csk_gram.argtypes = [P, i64, i64, P, P, i64, P, P, sz, P]
+        L.csk_gram.restype = ctypes.c_int
         L.csk_solve_host_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(csk_params)]
         L.csk_solve_host_workspace_size.restype = sz
         L.csk_solve_host.argtypes = [P, i64, i64, i64, P, i32, ctypes.POINTER(csk_params), P, P,
@@ -211,6 +215,27 @@ def csk_sketch(A: torch.Tensor, d: int, seed: int, b: torch.Tensor | None = None
     if bt is not None and b.dim() == 1:
         bt = bt[:, 0]
     return Sketch(At, bt, N2, P, O)
+
+
+def csk_gram(At: torch.Tensor, norms2: torch.Tensor | None = None, *, ldg: int | None = None,
+             info: torch.Tensor | None = None, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """G = At At^T in split BF16 on the tensor cores (d x d FP32; the
+    returned tensor is a d x d view of a d x ldg buffer)."""
+    dev = _check_cuda(At, norms2, info, ws)
+    if At.dtype != torch.float32 or not At.is_contiguous():
+        raise TypeError("At must be contiguous float32")
+    d, n = At.shape
+    if norms2 is not None and (norms2.dtype != torch.float64 or norms2.numel() != d):
+        raise TypeError("norms2 must be d float64 values")
+    ldg = ldg or (d + 31) // 32 * 32
+    G = torch.empty((d, ldg), dtype=torch.float32, device=dev)
+    if ws is None:
+        ws = _workspace(int(lib().csk_gram_workspace_size(d, n)), dev)
+    rc = lib().csk_gram(_ptr(At), d, n, _ptr(norms2), _ptr(G), ldg, _ptr(info), _ptr(ws),
+                        ws.numel(), _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_gram")
+    return G[:, :d]
 
 
 def csk_solve_workspace_size(m: int, n: int, dtype: int, params: csk_params) -> int:

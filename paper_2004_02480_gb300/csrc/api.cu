@@ -266,6 +266,26 @@ int csk_sketch(const void* A, int64_t m, int64_t n, int64_t lda, const void* B, 
     return CSK_OK;
 }
 
+size_t csk_gram_workspace_size(int64_t d, int64_t n) {
+    if (d < 1 || n < 1 || d > INT_MAX || n > INT_MAX) return 0;
+    return align256(gram_scratch_bytes((int)d, (int)n));
+}
+
+int csk_gram(const float* At, int64_t d, int64_t n, const double* norms2, float* G, int64_t ldg,
+             csk_info* info, void* ws, size_t ws_bytes, void* stream) {
+    if (!At || !G || !ws) return CSK_EINVAL;
+    if (d < 1 || n < 1 || ldg < d) return CSK_EINVAL;
+    if (d > INT_MAX || n > INT_MAX) return CSK_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    if (ws_bytes < csk_gram_workspace_size(d, n)) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    if (launch_gram_split_bf16(At, (int)d, (int)n, norms2, G, ldg, ws, info, st) != cudaSuccess)
+        return CSK_ECUDA;
+    return CSK_OK;
+}
+
 size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_params* params) {
     if (!params || m < 1 || n < 1 || params->d < 0) return 0;
     if (dtype != CSK_F32 && dtype != CSK_F64) return 0;

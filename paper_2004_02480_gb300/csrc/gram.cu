@@ -235,6 +235,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     const int good = __syncthreads_and(acc_ok && !fail_sh);   // uniform over the CTA
     tc_fence_after();
     const int row = bi * BM + warp * 32 + lane;
+    const bool vec_ok = (ldg % 4 == 0) && (reinterpret_cast<uintptr_t>(G) % 16 == 0);
     if (good) {
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -243,7 +244,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const int col0 = bj * BN + c0;
             if (row < d) {
                 float* dst = G + (int64_t)row * ldg + col0;
-                if (col0 + 32 <= d) {
+                if (vec_ok && col0 + 32 <= d) {
 #pragma unroll
                     for (int q = 0; q < 32; q += 4)
                         *reinterpret_cast<float4*>(dst + q) =
@@ -260,7 +261,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     if (col0 + q < d && row < d) G[(int64_t)(col0 + q) * ldg + row] = __uint_as_float(v[q]);
             }
         }
-    } else if (threadIdx.x == 0) {
+    } else if (threadIdx.x == 0 && info) {
         set_status_once(info, CSK_ETIMEOUT);
     }
     tc_fence_before();
@@ -336,8 +337,8 @@ cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* 
     if (e != cudaSuccess) return e;
     const int nt = dp / BM;
     k_gram_tc<<<dim3(nt, nt), 128, smem, st>>>(mh, ml, d, kp / BK, G, ldg, info);
-    k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
-    note_launches(3);
+    if (N2) k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
+    note_launches(N2 ? 3 : 2);
     return cudaGetLastError();
 }
 

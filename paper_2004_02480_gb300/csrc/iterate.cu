@@ -5,13 +5,20 @@
 // Each CTA owns a contiguous block of rows of At.  A step is
 //   Phase A  every CTA scores its rows, key_j = r_j^2 / ||At_j||^2, keeps its
 //            best (key, row, alpha = r_j / ||At_j||^2) and a partial of the
-//            stopping statistic, and publishes them in its slot (release);
-//   Phase B  every CTA waits for all slots of this round (acquire, bounded
-//            poll count), reduces them in the same fixed order -- so all CTAs
-//            take the same decision bit for bit -- tests the stopping rule of
-//            Section 3 and applies the projection of Algorithm 1.
-// One inter-CTA exchange per step; slots alternate between two banks so a
+//            stopping statistic, and publishes them in its slot;
+//   Phase B  every CTA waits for all slots of this round (bounded poll count),
+//            reduces them in one fixed order -- so every CTA takes the same
+//            decision bit for bit -- tests the stopping rule of Section 3 and
+//            applies the projection of Algorithm 1.
+// One inter-CTA exchange per step.  Slots alternate between two banks, so a
 // fast CTA can never overwrite a slot a slow CTA has still to read.
+//
+// FP32 solves keep every per-step operation in FP32 (this GPU's FP64 rate is
+// a small fraction of its FP32 rate): keys, step lengths and the stopping
+// statistic are FP32, and a slot is four 64-bit words that each carry the
+// round stamp next to 32 bits of payload, so one relaxed load of each word
+// both detects the new round and delivers its data (one L2 round trip).
+// FP64 solves use FP64 throughout and a release/acquire-stamped slot.
 //
 // GEMV path: r = bt - At x is recomputed every step (Algorithm 1 as printed);
 // x is replicated in every CTA's shared memory and, when it fits, the CTA's
@@ -30,71 +37,134 @@ namespace csk {
 namespace {
 
 constexpr int kIterThreads = 256;
+constexpr int kWarps = kIterThreads / 32;
 constexpr int kMaxGrid = 1024;
-constexpr int64_t kDefaultSpin = 1ll << 21;
+constexpr int64_t kDefaultSpin = 1ll << 22;
+constexpr int kRowsPerWarp = 4;          // rows a warp scores together (ILP)
 
-struct RedShared {
-    double key[32];
-    double alpha[32];
-    int32_t idx[32];
-    double sum[32];
-    double bkey, balpha, bsum;
-    int32_t bidx;
-};
-
-__device__ __forceinline__ void block_argmax(double& key, double& alpha, int32_t& idx,
-                                             RedShared& sr) {
-    warp_argmax(key, alpha, idx);
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    if (lane == 0) { sr.key[warp] = key; sr.alpha[warp] = alpha; sr.idx[warp] = idx; }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        double k = lane < nw ? sr.key[lane] : -1.0;
-        double a = lane < nw ? sr.alpha[lane] : 0.0;
-        int32_t i = lane < nw ? sr.idx[lane] : INT_MAX;
-        warp_argmax(k, a, i);
-        if (lane == 0) { sr.bkey = k; sr.balpha = a; sr.bidx = i; }
-    }
-    __syncthreads();
-    key = sr.bkey; alpha = sr.balpha; idx = sr.bidx;
-    __syncthreads();
+// ----------------------------------------------------- candidate algebra
+// Larger key wins; equal keys -> smaller row (first maximiser); NaN keys win
+// so that a numerical failure reaches the common decision.
+template <typename T>
+__device__ __forceinline__ bool better(T ka, int32_t ia, T kb, int32_t ib) {
+    const bool na = ka != ka, nb = kb != kb;
+    if (na != nb) return na;
+    if (na) return ia < ib;
+    return ka > kb || (ka == kb && ia < ib);
 }
 
-__device__ __forceinline__ double block_sum(double v, RedShared& sr) {
-    v = warp_sum(v);
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    if (lane == 0) sr.sum[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        double s = lane < nw ? sr.sum[lane] : 0.0;
-        s = warp_sum(s);
-        if (lane == 0) sr.bsum = s;
+template <typename T>
+struct Red {
+    T key, alpha, stat;
+    int32_t idx;
+};
+
+template <typename T>
+__device__ __forceinline__ void warp_reduce(Red<T>& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T k2 = __shfl_xor_sync(0xffffffffu, c.key, o);
+        const T a2 = __shfl_xor_sync(0xffffffffu, c.alpha, o);
+        const int32_t i2 = __shfl_xor_sync(0xffffffffu, c.idx, o);
+        c.stat += __shfl_xor_sync(0xffffffffu, c.stat, o);
+        if (better(k2, i2, c.key, c.idx)) { c.key = k2; c.alpha = a2; c.idx = i2; }
     }
+}
+
+// CTA-wide reduction with a single barrier: warps post their partial results
+// in one of two shared buffers (alternating between calls), then every warp
+// reduces the posted partials itself, so all threads end with the same bits.
+template <typename T>
+struct RedShared {
+    Red<T> buf[2][kWarps];
+};
+
+template <typename T>
+__device__ __forceinline__ Red<T> block_reduce(Red<T> c, RedShared<T>& sh, int& par) {
+    warp_reduce(c);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.buf[par][warp] = c;
     __syncthreads();
-    v = sr.bsum;
-    __syncthreads();
+    Red<T> r;
+    if (lane < kWarps) r = sh.buf[par][lane];
+    else { r.key = T(-1); r.alpha = T(0); r.stat = T(0); r.idx = INT_MAX; }
+    par ^= 1;
+    warp_reduce(r);
+    return r;
+}
+
+// ---------------------------------------------------------- exchanges
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Publish this CTA's candidate for `round` and gather every CTA's.  Returns
-// false when a wait ran out of polls (status CSK_ETIMEOUT recorded).
-__device__ bool exchange(Slot* slots, uint32_t round, double& key, double& alpha, int32_t& idx,
-                         double& stat, int64_t spin_limit, int fault_inject, csk_info* info,
-                         RedShared& sr) {
+// FP32: four stamped words per slot.
+// With `acquire`, every polling thread fences after seeing the new round, so
+// plain data the other CTAs stored before publishing is visible afterwards.
+__device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>& c,
+                                         int64_t spin_limit, int fault_inject, csk_info* info,
+                                         RedShared<float>& sh, int& par, bool acquire = false) {
+    const int G = gridDim.x, b = blockIdx.x;
+    uint64_t* bank = reinterpret_cast<uint64_t*>(slots + (size_t)(round & 1u) * G);
+    const uint64_t stamp = (uint64_t)(round + 1u) << 32;
+    if (threadIdx.x == 0 && !(fault_inject && b == 0)) {
+        uint64_t* w = bank + 4 * b;
+        st_relaxed_u64(w + 0, stamp | __float_as_uint(c.key));
+        st_relaxed_u64(w + 1, stamp | __float_as_uint(c.alpha));
+        st_relaxed_u64(w + 2, stamp | __float_as_uint(c.stat));
+        st_relaxed_u64(w + 3, stamp | (uint32_t)c.idx);
+    }
+    Red<float> g;
+    g.key = -1.0f; g.alpha = 0.0f; g.stat = 0.0f; g.idx = INT_MAX;
+    int timed_out = 0;
+    for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        const uint64_t* w = bank + 4 * t;
+        uint64_t v0, v1, v2, v3;
+        int64_t spins = 0;
+        for (;;) {
+            v0 = ld_relaxed_u64(w + 0);
+            v1 = ld_relaxed_u64(w + 1);
+            v2 = ld_relaxed_u64(w + 2);
+            v3 = ld_relaxed_u64(w + 3);
+            const uint64_t hi = stamp >> 32;
+            if ((v0 >> 32) == hi && (v1 >> 32) == hi && (v2 >> 32) == hi && (v3 >> 32) == hi) break;
+            if (++spins > spin_limit) { timed_out = 1; break; }
+        }
+        if (timed_out) break;
+        if (acquire) __threadfence();
+        const float k2 = __uint_as_float((uint32_t)v0);
+        const int32_t i2 = (int32_t)(uint32_t)v3;
+        g.stat += __uint_as_float((uint32_t)v2);
+        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = __uint_as_float((uint32_t)v1); g.idx = i2; }
+    }
+    if (__syncthreads_or(timed_out)) {
+        if (threadIdx.x == 0) set_status_once(info, CSK_ETIMEOUT);
+        return false;
+    }
+    c = block_reduce(g, sh, par);
+    return true;
+}
+
+// FP64: payload, then a release-stamped word; readers acquire the stamp.
+__device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<double>& c,
+                                         int64_t spin_limit, int fault_inject, csk_info* info,
+                                         RedShared<double>& sh, int& par) {
     const int G = gridDim.x, b = blockIdx.x;
     Slot* bank = slots + (size_t)(round & 1u) * G;
     if (threadIdx.x == 0 && !(fault_inject && b == 0)) {
-        bank[b].key = key;
-        bank[b].alpha = alpha;
-        bank[b].stat = stat;
-        bank[b].idx = idx;
-        __threadfence();
+        bank[b].key = c.key;
+        bank[b].alpha = c.alpha;
+        bank[b].stat = c.stat;
+        bank[b].idx = c.idx;
         st_release_u32(&bank[b].stamp, round + 1u);
     }
-    double gk = -1.0, ga = 0.0, gs = 0.0;
-    int32_t gi = INT_MAX;
+    Red<double> g;
+    g.key = -1.0; g.alpha = 0.0; g.stat = 0.0; g.idx = INT_MAX;
     int timed_out = 0;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
         int64_t spins = 0;
@@ -102,32 +172,28 @@ __device__ bool exchange(Slot* slots, uint32_t round, double& key, double& alpha
             if (++spins > spin_limit) { timed_out = 1; break; }
         }
         if (timed_out) break;
-        // payload read through L2: the line may be stale in L1 from two rounds ago
         const double k2 = __ldcg(&bank[t].key);
-        const double a2 = __ldcg(&bank[t].alpha);
         const int32_t i2 = __ldcg(&bank[t].idx);
-        gs += __ldcg(&bank[t].stat);
-        if (cand_better(k2, i2, gk, gi)) { gk = k2; ga = a2; gi = i2; }
+        g.stat += __ldcg(&bank[t].stat);
+        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = __ldcg(&bank[t].alpha); g.idx = i2; }
     }
     if (__syncthreads_or(timed_out)) {
         if (threadIdx.x == 0) set_status_once(info, CSK_ETIMEOUT);
         return false;
     }
-    block_argmax(gk, ga, gi, sr);
-    gs = block_sum(gs, sr);
-    key = gk; alpha = ga; idx = gi; stat = gs;
+    c = block_reduce(g, sh, par);
     return true;
 }
 
 // Decision shared by every CTA after an exchange (Section 3 stopping rule,
 // tested before the step).  Returns a csk_status to stop with, or INT_MIN to
 // continue.
-__device__ __forceinline__ int decide(double stat, double stop_norm, double tol, int64_t k,
-                                      int64_t max_iter, double key) {
-    if (stat / stop_norm <= tol) return CSK_OK;
+template <typename T>
+__device__ __forceinline__ int decide(T stat, T threshold, int64_t k, int64_t max_iter, T key) {
+    if (stat <= threshold) return CSK_OK;
     if (k >= max_iter) return CSK_MAXITER;
-    if (key != key || key < 0.0) return CSK_ENUMERIC;   // NaN, or no non-zero row
-    if (key == 0.0) return CSK_OK;                       // every residual is exactly 0
+    if (key != key || key < T(0)) return CSK_ENUMERIC;   // NaN, or no non-zero row
+    if (key == T(0)) return CSK_OK;                      // every residual is exactly 0
     return INT_MIN;
 }
 
@@ -138,22 +204,32 @@ __device__ __forceinline__ void finish(csk_info* info, int status, int64_t k) {
     }
 }
 
+template <typename T>
+__device__ __forceinline__ T weight_of(double N) {
+    // 1/||At_j||^2; -1 marks a zero row (excluded from the argmax); NaN (a
+    // NaN/Inf row) is kept so that the failure reaches the decision
+    return N > 0.0 ? (T)(1.0 / N) : (N == 0.0 ? T(-1) : (T)NAN);
+}
+
 // ------------------------------------------------------------ GEMV path
+// Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
 template <typename T>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ RedShared sr;
+    __shared__ RedShared<T> sh;
+    int par = 0;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-    const int lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     const int n = p.n, d = p.d;
     const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
     const int c0 = (int)((int64_t)n * b / G), c1 = (int)((int64_t)n * (b + 1) / G);
-    const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3;
+    const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3, spad = ((n + G - 1) / G + 4) & ~3;
     T* xs = reinterpret_cast<T*>(dsm);
     T* w2s = xs + npad;
     T* bts = w2s + Rpad;
-    T* As = bts + Rpad;
+    T* xss = bts + Rpad;
+    T* As = xss + spad;
     const T* At = static_cast<const T*>(p.At);
     const T* bt = static_cast<const T*>(p.bt);
     const T* x0 = static_cast<const T*>(p.x0);
@@ -161,107 +237,118 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
 
     for (int c = tid; c < n; c += blockDim.x) xs[c] = x0 ? x0[c] : T(0);
     for (int q = tid; q < nr; q += blockDim.x) {
-        // weight 1/||At_j||^2; -1 marks a zero row (excluded from the argmax),
-        // NaN (a NaN/Inf row) is kept so that the failure reaches the decision
-        const double N = p.N2[r0 + q];
-        w2s[q] = N > 0.0 ? (T)(1.0 / N) : (N == 0.0 ? T(-1) : (T)NAN);
+        w2s[q] = weight_of<T>(p.N2[r0 + q]);
         bts[q] = bt[r0 + q];
     }
-    if (cache_rows) {
+    if (xstar)
+        for (int c = c0 + tid; c < c1; c += blockDim.x) xss[c - c0] = xstar[c];
+    if (cache_rows)
         for (int64_t e = tid; e < (int64_t)nr * n; e += blockDim.x) {
             const int q = (int)(e / n), c = (int)(e - (int64_t)q * n);
             As[e] = At[(int64_t)(r0 + q) * p.ld + c];
         }
-    }
     __syncthreads();
-    const double stop_norm = *p.stop_norm;
+    const T threshold = (T)(p.tol * *p.stop_norm);   // RES <= tol  <=>  stat <= tol ||x*||^2
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    const int64_t lda = cache_rows ? (int64_t)n : p.ld;
+    const T* Abase = cache_rows ? As : At + (int64_t)r0 * p.ld;
     uint32_t round = 0;
     int64_t k = 0;
     int status = CSK_OK;
     for (;;) {
-        // Phase A: residuals of the owned rows and the CTA's best row
-        double bkey = -1.0, balpha = 0.0, stat = 0.0;
-        int32_t bidx = INT_MAX;
-        for (int q = warp; q < nr; q += nw) {
-            const T* a = cache_rows ? As + (int64_t)q * n : At + (int64_t)(r0 + q) * p.ld;
-            T acc = T(0);
-            for (int c = lane; c < n; c += 32) acc = fma(a[c], xs[c], acc);
-            acc = warp_sum(acc);
-            const T r = bts[q] - acc;
-            if (lane == 0) {
-                const T w = w2s[q];
-                if (!(w < T(0))) {
-                    const double key = (double)(r * r * w);
-                    if (cand_better(key, r0 + q, bkey, bidx)) {
-                        bkey = key;
-                        balpha = (double)r / p.N2[r0 + q];
-                        bidx = r0 + q;
+        // Phase A: residuals of the owned rows, kRowsPerWarp rows at a time
+        Red<T> c;
+        c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
+        for (int q0 = warp * kRowsPerWarp; q0 < nr; q0 += kWarps * kRowsPerWarp) {
+            T acc[kRowsPerWarp];
+            const T* a[kRowsPerWarp];
+#pragma unroll
+            for (int u = 0; u < kRowsPerWarp; ++u) {
+                acc[u] = T(0);
+                a[u] = Abase + (int64_t)min(q0 + u, nr - 1) * lda;
+            }
+            for (int col = lane; col < n; col += 32) {
+                const T xv = xs[col];
+#pragma unroll
+                for (int u = 0; u < kRowsPerWarp; ++u) acc[u] = fma(a[u][col], xv, acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kRowsPerWarp; ++u) {
+                const T dot = warp_sum(acc[u]);
+                const int q = q0 + u;
+                if (q < nr) {
+                    const T r = bts[q] - dot;
+                    const T w = w2s[q];
+                    if (!(w < T(0))) {
+                        const T key = r * r * w;
+                        if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
                     }
+                    if (!xstar && lane == 0) c.stat += r * r;
                 }
-                if (!xstar) stat += (double)r * (double)r;
             }
         }
         if (xstar)
-            for (int c = c0 + tid; c < c1; c += blockDim.x) {
-                const double t = (double)xs[c] - (double)xstar[c];
-                stat += t * t;
+            for (int col = c0 + tid; col < c1; col += blockDim.x) {
+                const T t = xs[col] - xss[col - c0];
+                c.stat += t * t;
             }
-        block_argmax(bkey, balpha, bidx, sr);
-        stat = block_sum(stat, sr);
+        c = block_reduce(c, sh, par);
         // Phase B
-        if (!exchange(p.slots, round, bkey, balpha, bidx, stat, spin, p.fault_inject, p.info, sr)) {
+        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
         }
         ++round;
-        const int dec = decide(stat, stop_norm, p.tol, k, p.max_iter, bkey);
+        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
         if (dec != INT_MIN) { status = dec; break; }
-        if (b == 0 && tid == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = bidx;
+        if (b == 0 && tid == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
         if (b == 0 && p.x_log && k < p.x_log_len)
-            for (int c = tid; c < n; c += blockDim.x) static_cast<T*>(p.x_log)[k * n + c] = xs[c];
+            for (int col = tid; col < n; col += blockDim.x) static_cast<T*>(p.x_log)[k * n + col] = xs[col];
         // projection onto row i_k: x += alpha * At_{i_k}^T (same in every CTA)
-        const T al = (T)balpha;
-        const T* arow = At + (int64_t)bidx * p.ld;
-        for (int c = tid; c < n; c += blockDim.x) xs[c] = fma(al, arow[c], xs[c]);
+        const T* arow = At + (int64_t)c.idx * p.ld;
+        for (int col = tid; col < n; col += blockDim.x) xs[col] = fma(c.alpha, __ldg(arow + col), xs[col]);
         __syncthreads();
         ++k;
     }
     if (b == 0) {
         T* xo = static_cast<T*>(p.x_out);
-        for (int c = tid; c < n; c += blockDim.x) xo[c] = xs[c];
+        for (int col = tid; col < n; col += blockDim.x) xo[col] = xs[col];
     }
     finish(p.info, status, k);
 }
 
 // ------------------------------------------------------------ GRAM path
+// Shared memory: r (Rpad) | w2 (Rpad) | x slice (spad) | x* slice (spad) |
+// full x for the refresh (npad)
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gram(IterProblem p, int R) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ RedShared sr;
+    __shared__ RedShared<float> sh;
+    int par = 0;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-    const int lane = lane_id(), warp = tid >> 5, nw = blockDim.x >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
     const int n = p.n, d = p.d;
     const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
     const int c0 = (int)((int64_t)n * b / G), c1 = (int)((int64_t)n * (b + 1) / G);
-    const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3;
-    float* rs = reinterpret_cast<float*>(dsm);           // Rpad
-    float* w2s = rs + Rpad;                              // Rpad
-    float* xsl = w2s + Rpad;                             // npad (slice used)
-    float* xfull = xsl + npad;                           // npad
+    const int Rpad = (R + 3) & ~3, spad = ((n + G - 1) / G + 4) & ~3;
+    float* rs = reinterpret_cast<float*>(dsm);
+    float* w2s = rs + Rpad;
+    float* xsl = w2s + Rpad;
+    float* xss = xsl + spad;
+    float* xfull = xss + spad;
     const float* At = static_cast<const float*>(p.At);
     const float* bt = static_cast<const float*>(p.bt);
     const float* x0 = static_cast<const float*>(p.x0);
     const float* xstar = static_cast<const float*>(p.xstar);
     float* xg = static_cast<float*>(p.xg);
 
-    for (int c = c0 + tid; c < c1; c += blockDim.x) xsl[c - c0] = x0 ? x0[c] : 0.0f;
-    for (int q = tid; q < nr; q += blockDim.x) {
-        const double N = p.N2[r0 + q];
-        w2s[q] = N > 0.0 ? (float)(1.0 / N) : (N == 0.0 ? -1.0f : NAN);
+    for (int c = c0 + tid; c < c1; c += blockDim.x) {
+        xsl[c - c0] = x0 ? x0[c] : 0.0f;
+        if (xstar) xss[c - c0] = xstar[c];
     }
+    for (int q = tid; q < nr; q += blockDim.x) w2s[q] = weight_of<float>(p.N2[r0 + q]);
     __syncthreads();
-    const double stop_norm = *p.stop_norm;
+    const float threshold = (float)(p.tol * *p.stop_norm);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     const int K = p.refresh_every;
     uint32_t round = 0;
@@ -269,19 +356,22 @@ k_iterate_gram(IterProblem p, int R) {
     int status = CSK_OK;
     for (;;) {
         if (k == 0 || (K > 0 && k % K == 0)) {
-            // FP64 refresh r = bt - At x: gather the x slices first
+            // FP64 refresh r = bt - At x: gather the x slices first; the
+            // fence orders this CTA's slice stores before its slot words
             for (int c = c0 + tid; c < c1; c += blockDim.x) xg[c] = xsl[c - c0];
-            double dk = 0.0, da = 0.0, ds = 0.0;
-            int32_t di = 0;
+            __threadfence();
             __syncthreads();
-            if (!exchange(p.slots, round, dk, da, di, ds, spin, p.fault_inject, p.info, sr)) {
+            Red<float> dummy;
+            dummy.key = -1.0f; dummy.alpha = 0.0f; dummy.stat = 0.0f; dummy.idx = INT_MAX;
+            if (!exchange(p.slots, round, dummy, spin, p.fault_inject, p.info, sh, par, true)) {
                 status = CSK_ETIMEOUT;
                 break;
             }
             ++round;
+            __threadfence();
             for (int c = tid; c < n; c += blockDim.x) xfull[c] = __ldcg(xg + c);
             __syncthreads();
-            for (int q = warp; q < nr; q += nw) {
+            for (int q = warp; q < nr; q += kWarps) {
                 const float* a = At + (int64_t)(r0 + q) * p.ld;
                 double acc = 0.0;
                 for (int c = lane; c < n; c += 32) acc = fma((double)a[c], (double)xfull[c], acc);
@@ -291,65 +381,70 @@ k_iterate_gram(IterProblem p, int R) {
             __syncthreads();
         }
         // Phase A
-        double bkey = -1.0, balpha = 0.0, stat = 0.0;
-        int32_t bidx = INT_MAX;
+        Red<float> c;
+        c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
         for (int q = tid; q < nr; q += blockDim.x) {
             const float r = rs[q], w = w2s[q];
             if (!(w < 0.0f)) {
-                const double key = (double)(r * r * w);
-                if (cand_better(key, r0 + q, bkey, bidx)) {
-                    bkey = key;
-                    balpha = (double)r / p.N2[r0 + q];
-                    bidx = r0 + q;
-                }
+                const float key = r * r * w;
+                if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
             }
-            if (!xstar) stat += (double)r * (double)r;
+            if (!xstar) c.stat += r * r;
         }
         if (xstar)
-            for (int c = c0 + tid; c < c1; c += blockDim.x) {
-                const double t = (double)xsl[c - c0] - (double)xstar[c];
-                stat += t * t;
+            for (int col = c0 + tid; col < c1; col += blockDim.x) {
+                const float t = xsl[col - c0] - xss[col - c0];
+                c.stat += t * t;
             }
-        block_argmax(bkey, balpha, bidx, sr);
-        stat = block_sum(stat, sr);
-        if (!exchange(p.slots, round, bkey, balpha, bidx, stat, spin, p.fault_inject, p.info, sr)) {
+        c = block_reduce(c, sh, par);
+        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
         }
         ++round;
-        const int dec = decide(stat, stop_norm, p.tol, k, p.max_iter, bkey);
+        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
         if (dec != INT_MIN) { status = dec; break; }
-        if (b == 0 && tid == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = bidx;
+        if (b == 0 && tid == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
         if (p.x_log && k < p.x_log_len)
-            for (int c = c0 + tid; c < c1; c += blockDim.x)
-                static_cast<float*>(p.x_log)[k * n + c] = xsl[c - c0];
+            for (int col = c0 + tid; col < c1; col += blockDim.x)
+                static_cast<float*>(p.x_log)[k * n + col] = xsl[col - c0];
         // r -= alpha G[i_k, :] on the owned rows, r_{i_k} = 0 exactly;
         // x slice += alpha At_{i_k}
-        const float al = (float)balpha;
-        const float* grow = p.G + (int64_t)bidx * p.ldg;
+        const float* grow = p.G + (int64_t)c.idx * p.ldg;
         for (int q = tid; q < nr; q += blockDim.x) {
             const int j = r0 + q;
-            rs[q] = (j == bidx) ? 0.0f : fmaf(-al, grow[j], rs[q]);
+            rs[q] = (j == c.idx) ? 0.0f : fmaf(-c.alpha, __ldg(grow + j), rs[q]);
         }
-        const float* arow = At + (int64_t)bidx * p.ld;
-        for (int c = c0 + tid; c < c1; c += blockDim.x) xsl[c - c0] = fmaf(al, arow[c], xsl[c - c0]);
+        const float* arow = At + (int64_t)c.idx * p.ld;
+        for (int col = c0 + tid; col < c1; col += blockDim.x)
+            xsl[col - c0] = fmaf(c.alpha, __ldg(arow + col), xsl[col - c0]);
         __syncthreads();
         ++k;
     }
     float* xo = static_cast<float*>(p.x_out);
-    for (int c = c0 + tid; c < c1; c += blockDim.x) xo[c] = xsl[c - c0];
+    for (int col = c0 + tid; col < c1; col += blockDim.x) xo[col] = xsl[col - c0];
     finish(p.info, status, k);
 }
 
 // --------------------------------------------------------- final check
 constexpr int kFinalThreads = 256;
 
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+    v = warp_sum(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    return warp_sum(s);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFinalThreads)
 k_final_rows(const T* __restrict__ At, int64_t ld, int d, int n, const T* __restrict__ bt,
              const double* __restrict__ N2, const T* __restrict__ x, double* __restrict__ part) {
-    __shared__ RedShared sr;
-    const int lane = lane_id();
+    __shared__ double sh[32];
+    const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     double rr = 0.0, bb = 0.0, empty = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < d; j += nwarps) {
@@ -363,9 +458,9 @@ k_final_rows(const T* __restrict__ At, int64_t ld, int d, int n, const T* __rest
             empty += (N2[j] > 0.0) ? 0.0 : 1.0;
         }
     }
-    rr = block_sum(rr, sr);
-    bb = block_sum(bb, sr);
-    empty = block_sum(empty, sr);
+    rr = block_sum_f64(rr, sh);
+    bb = block_sum_f64(bb, sh);
+    empty = block_sum_f64(empty, sh);
     if (threadIdx.x == 0) {
         part[3 * blockIdx.x + 0] = rr;
         part[3 * blockIdx.x + 1] = bb;
@@ -377,7 +472,7 @@ template <typename T>
 __global__ void __launch_bounds__(kFinalThreads)
 k_final_reduce(const double* __restrict__ part, int nparts, const T* __restrict__ x,
                const T* __restrict__ xstar, int n, csk_info* info) {
-    __shared__ RedShared sr;
+    __shared__ double sh[32];
     double rr = 0.0, bb = 0.0, empty = 0.0, ee = 0.0, ss = 0.0;
     for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
         rr += part[3 * t];
@@ -390,11 +485,11 @@ k_final_reduce(const double* __restrict__ part, int nparts, const T* __restrict_
             ee += e * e;
             ss += (double)xstar[c] * (double)xstar[c];
         }
-    rr = block_sum(rr, sr);
-    bb = block_sum(bb, sr);
-    empty = block_sum(empty, sr);
-    ee = block_sum(ee, sr);
-    ss = block_sum(ss, sr);
+    rr = block_sum_f64(rr, sh);
+    bb = block_sum_f64(bb, sh);
+    empty = block_sum_f64(empty, sh);
+    ee = block_sum_f64(ee, sh);
+    ss = block_sum_f64(ss, sh);
     if (threadIdx.x == 0) {
         info->resid = sqrt(rr / bb);
         info->rse = xstar ? ee / ss : (double)NAN;
@@ -430,15 +525,15 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cf
         if (want < G) G = (int)want;
     }
     const int R = (d + G - 1) / G;
-    const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3;
+    const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3, spad = ((n + G - 1) / G + 4) & ~3;
     cfg->grid = G;
     cfg->threads = kIterThreads;
     cfg->rows_per_cta = R;
     if (path == CSK_RESID_GRAM) {
         cfg->cache_rows = 0;
-        cfg->smem = (size_t)(2 * Rpad + 2 * npad) * 4;
+        cfg->smem = (size_t)(2 * Rpad + 2 * spad + npad) * 4;
     } else {
-        const size_t base = (size_t)(npad + 2 * Rpad) * s;
+        const size_t base = (size_t)(npad + 2 * Rpad + spad) * s;
         const size_t rows = (size_t)R * n * s;
         cfg->cache_rows = (base + rows <= budget) ? 1 : 0;
         cfg->smem = base + (cfg->cache_rows ? rows : 0);

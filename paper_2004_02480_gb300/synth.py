@@ -87,3 +87,26 @@ def batched_shapes(S: int, m_lo: int, m_hi: int, n_lo: int, n_hi: int, seed: int
     m = np.exp(g.uniform(np.log(m_lo), np.log(m_hi), S)).astype(np.int64)
     n = g.integers(n_lo, n_hi + 1, S)
     return [(int(a), int(c)) for a, c in zip(m, n)]
+
+
+def conditioned_system_device(m: int, n: int, seed: int, kappa: float = 1e3, device="cuda",
+                              block: int = 131072):
+    """conditioned_system() drawn on a torch device (for sizes where host
+    generation is slow): A = G diag(sigma) Q in FP32, G from a seeded torch
+    generator on the device, Q Haar (host QR), x* N(0,1), b = A x* with
+    binary64 accumulation.  Returns (A, b, x_star) torch tensors."""
+    import torch
+    g = _rng(seed)
+    Q = haar_orthogonal(n, g)
+    sig = kappa ** (np.arange(n) / max(n - 1, 1))
+    M = torch.from_numpy(sig[:, None] * Q).to(device=device, dtype=torch.float32)
+    xs = torch.from_numpy(g.standard_normal(n)).to(device)
+    tg = torch.Generator(device=device).manual_seed(int(seed) * 7919 + 17)
+    A = torch.empty((m, n), dtype=torch.float32, device=device)
+    b = torch.empty(m, dtype=torch.float32, device=device)
+    for s in range(0, m, block):
+        e = min(m, s + block)
+        Gb = torch.randn((e - s, n), generator=tg, device=device, dtype=torch.float32)
+        A[s:e] = Gb @ M
+        b[s:e] = (A[s:e].double() @ xs).float()
+    return A, b, xs

@@ -1,0 +1,155 @@
+"""GPU parity of the split-BF16 Gram matrix (tcgen05) and of the GRAM residual
+path of the iteration.
+
+Tolerances (derived, not tuned):
+* GPU G against the oracle's split product (the same BF16 operands, summed
+  exactly in binary64): the only difference is FP32 accumulation of K = 3n
+  products; with random signs its error is ~ K u |term| = 3 u (|A||A|^T)_ij
+  (u = 2^-24), so |G - G_split| <= 2^-17 (|A||A|^T)_ij leaves an 8x margin,
+  while a dropped hi*lo term would be ~2^-9 / sqrt(n) of (|A||A|^T)_ij.
+* GPU G against the exact product: the split drops lo*lo and rounds lo,
+  2^-16 relative per product, so |G - A A^T| <= 2^-14 (|A||A|^T)_ij.
+* G is exactly symmetric and G_jj = fl32(||A_j||^2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_02480_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def csk():
+    from paper_2004_02480_gb300 import build, csk as _csk
+    build.build()
+    return _csk
+
+
+def _check_G(G, At, rows=None, Gs_rows=None):
+    A64 = At.astype(np.float64)
+    rows = np.arange(At.shape[0]) if rows is None else np.asarray(rows)
+    Gs = oracle.gram_split_bf16(At) if Gs_rows is None else Gs_rows
+    if Gs_rows is None:
+        Gs = Gs[rows]
+    scale = np.abs(A64[rows]) @ np.abs(A64).T
+    exact = A64[rows] @ A64.T
+    Gr = G[rows].astype(np.float64)
+    assert np.all(np.abs(Gr - Gs) <= 2.0 ** -17 * scale)
+    assert np.all(np.abs(Gr - exact) <= 2.0 ** -14 * scale)
+
+
+@pytest.mark.parametrize("d,n", [(1, 1), (5, 3), (300, 70), (1000, 256), (129, 65), (777, 1000)])
+def test_gram_matches_split_oracle(csk, d, n):
+    rng = np.random.default_rng(d * 1000 + n)
+    At = rng.standard_normal((d, n)).astype(np.float32)
+    At_t = torch.from_numpy(At).to(DEV)
+    N2 = torch.from_numpy(oracle.row_norms2(At)).to(DEV)
+    G = csk.csk_gram(At_t, N2).cpu().numpy()
+    G_nodiag = csk.csk_gram(At_t).cpu().numpy()
+    torch.cuda.synchronize()
+    assert np.array_equal(G, G.T)                                   # mirrored tiles
+    assert np.array_equal(np.diag(G), oracle.row_norms2(At).astype(np.float32))
+    off = ~np.eye(d, dtype=bool)
+    assert np.array_equal(G[off], G_nodiag[off])
+    _check_G(G_nodiag, At)
+
+
+def test_gram_full_precision_form_sampled_rows(csk):
+    """d = 20000, n = 1000 (the precision-form sketch size): sampled rows."""
+    d, n = 20000, 1000
+    g = torch.Generator(device=DEV).manual_seed(3)
+    At_t = torch.randn((d, n), generator=g, device=DEV, dtype=torch.float32)
+    G = csk.csk_gram(At_t)
+    torch.cuda.synchronize()
+    At = At_t.cpu().numpy()
+    rows = np.random.default_rng(0).choice(d, 12, replace=False)
+    rows = np.concatenate([rows, [0, d - 1, 127, 128, 19999 - 128]])
+    Gs = oracle.gram_split_bf16_rows(At, rows)
+    Gh = G[torch.from_numpy(rows).to(DEV)].cpu().numpy()
+    full = np.zeros((d, d), np.float32)
+    full[rows] = Gh
+    _check_G(full, At, rows=rows, Gs_rows=Gs)
+    # symmetry on the sampled rows against the matching columns
+    Gc = G[:, torch.from_numpy(rows).to(DEV)].cpu().numpy().T
+    assert np.array_equal(Gh, Gc)
+
+
+def _solve(csk, s, d, seed, **kw):
+    A, b = torch.from_numpy(s.A).to(DEV), torch.from_numpy(s.b).to(DEV)
+    xs = torch.from_numpy(s.x_star.astype(np.float32)).to(DEV)
+    ik = torch.full((20000,), -1, dtype=torch.int32, device=DEV)
+    p = csk.csk_params_default(d=d, seed=seed, ik_log=ik.data_ptr(), ik_log_len=20000, **kw)
+    x, info = csk.csk_solve(A, b, p, x_star=xs)
+    return x.cpu().numpy(), info, ik.cpu().numpy()
+
+
+@pytest.mark.parametrize("refresh", [0, 50])
+def test_gram_path_converges_like_oracle(csk, refresh):
+    """GRAM path on 100000 x 500, d = 5000: RES <= 1e-6, i_k prefix equal to
+    the FP64 oracle's up to the first near-tie, IT within 5 %."""
+    m, n, d, seed = 100000, 500, 5000, 2
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x, info, ik = _solve(csk, s, d, seed, path=csk.GRAM, refresh_every=refresh)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At.astype(np.float64), bt.astype(np.float64), x_star=s.x_star,
+                      log_len=20000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6 and info["path"] == csk.GRAM
+    gap = ref.gap
+    k_tau = int(np.argmax(gap < 1e-3)) if np.any(gap < 1e-3) else len(gap)
+    K = min(1000, k_tau, ref.iters)
+    assert np.array_equal(ik[:K], ref.ik[:K])
+    assert abs(info["iters"] - ref.iters) <= 0.05 * ref.iters
+
+
+def test_gram_path_small_and_ragged(csk):
+    for (m, n, d) in [(5000, 70, 300), (3000, 1, 10), (20000, 129, 1000)]:
+        s = synth.gaussian_system(m, n, n, np.float32)
+        x, info, _ = _solve(csk, s, d, 4, path=csk.GRAM, refresh_every=25)
+        h, sg = oracle.count_sketch_map(4, m, d)
+        At, bt = oracle.sketch(s.A.astype(np.float64), s.b.astype(np.float64), h, sg, d)
+        ref = oracle.mwrk(At, bt, x_star=s.x_star)
+        assert info["status"] == ref.status == 0 and info["rse"] <= 1e-6
+        assert abs(info["iters"] - ref.iters) <= max(3, 0.1 * ref.iters)
+
+
+def test_precision_form_full_size(csk):
+    """The precision-form workload: A 1e6 x 1000 = G diag(sigma) Q (sigma
+    log-spaced 1..1e3), d = 20000, GRAM path with FP64 refresh every 100
+    steps.  With kappa = 1e3 RES <= 1e-6 lies far beyond the 20000-step cap
+    of Section 3, so the solve ends at the cap; checked: the status, the FP64
+    final RES against a host recomputation, monotone decrease of the error,
+    and the first 200 steps against the FP64 oracle on the same sketch."""
+    m, n, d, seed = 1_000_000, 1000, 20000, 0
+    A, b, xs64 = synth.conditioned_system_device(m, n, seed, 1e3, DEV)
+    xs = xs64.float()
+    L = 20000
+    X = torch.zeros((L, n), dtype=torch.float32, device=DEV)
+    ik = torch.full((L,), -1, dtype=torch.int32, device=DEV)
+    p = csk.csk_params_default(d=d, seed=seed, path=csk.GRAM, refresh_every=100, max_iter=L,
+                               ik_log=ik.data_ptr(), ik_log_len=L, x_log=X.data_ptr(), x_log_len=L)
+    x, info = csk.csk_solve(A, b, p, x_star=xs)
+    assert info["status"] == 1 and info["iters"] == L
+    xs_h = xs.double().cpu().numpy()
+    xh = x.double().cpu().numpy()
+    rse = np.sum((xh - xs_h) ** 2) / np.sum(xs_h ** 2)
+    assert abs(info["rse"] - rse) <= 1e-9 * rse
+    Xh = X.double().cpu().numpy()
+    e2 = np.sum((Xh - xs_h) ** 2, axis=1)
+    assert e2[-1] < 0.5 * e2[0]
+    # exact projections never increase the error; allow FP32 noise
+    assert np.all(e2[1:] <= e2[:-1] * (1 + 1e-4))
+    # first 200 steps against the FP64 oracle on the GPU's (bit-exact) sketch
+    sk = csk.csk_sketch(A, d, seed, b)
+    At = sk.At.double().cpu().numpy()
+    bt = sk.bt.double().cpu().numpy()
+    ref = oracle.mwrk(At, bt, x_star=xs_h, tol=0.0, max_iter=200, log_len=201, nthreads=16)
+    gap = ref.gap
+    k_tau = int(np.argmax(gap < 1e-3)) if np.any(gap < 1e-3) else len(gap)
+    K = min(200, k_tau)
+    assert np.array_equal(ik.cpu().numpy()[:K], ref.ik[:K])
+    assert abs(e2[200] - ref.err2[200]) <= 0.1 * ref.err2[200]
