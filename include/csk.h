@@ -146,6 +146,33 @@ int csk_sketch(const void *A, int64_t m, int64_t n, int64_t lda,
                void *ws, size_t ws_bytes, void *stream);
 
 /* ----------------------------------------------------------------------
+ * csk_sketch_noalloc -- csk_sketch without a workspace argument.
+ *
+ * The paper has no counterpart: this is a packaging variant for callers
+ * that cannot allocate device memory -- code handed only input and output
+ * pointers by a host application that owns all device memory (a plugin or
+ * callback with no allocator in its interface), or latency-critical code
+ * that must not call cudaMalloc because it can synchronise the device and
+ * take driver-wide locks.  Arguments and results are those of csk_sketch;
+ * the counting-sort scratch lives instead in one static device array of
+ * about 10 MB, which every GPU that loads the library holds until the
+ * process exits.  The call allocates nothing.
+ * Limits: m <= 1,048,576 rows and d <= 262,144 buckets; larger sizes return
+ * CSK_ENOMEM before anything is enqueued.
+ * The first call on a device looks up the array's device address for that
+ * device (a one-time host-side set-up); make that first call before any
+ * stream capture.  Every call shares the one array (it keeps the last
+ * call's contents; what must start at zero is cleared by each call), so
+ * calls whose GPU work overlaps -- on different streams, or from different
+ * host threads -- race and give wrong results.  Serialise them.
+ * -------------------------------------------------------------------- */
+int csk_sketch_noalloc(const void *A, int64_t m, int64_t n, int64_t lda,
+                       const void *B, int64_t ldb, int32_t nrhs, int32_t dtype,
+                       int64_t d, uint64_t seed,
+                       void *At, void *Bt, double *norms2_out,
+                       int32_t *perm_out, int32_t *off_out, void *stream);
+
+/* ----------------------------------------------------------------------
  * csk_gram -- G = At At^T (d x d, FP32) on the tensor cores, split BF16.
  *
  * The residual of Algorithm 1 after the projection onto row i_k changes by

@@ -84,6 +84,9 @@ def lib():
         L.csk_gram_workspace_size.restype = sz
         L.csk_gram.argtypes = [P, i64, i64, P, P, i64, P, P, sz, P]
         L.csk_gram.restype = ctypes.c_int
+        L.csk_sketch_noalloc.argtypes = [P, i64, i64, i64, P, i64, i32, i32, i64, u64, P, P, P,
+                                         P, P, P]
+        L.csk_sketch_noalloc.restype = ctypes.c_int
         L.csk_solve_host_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(csk_params)]
         L.csk_solve_host_workspace_size.restype = sz
         L.csk_solve_host.argtypes = [P, i64, i64, i64, P, i32, ctypes.POINTER(csk_params), P, P,
@@ -314,3 +317,35 @@ def csk_solve_host(A: np.ndarray, b: np.ndarray, params: csk_params, x0=None, x_
         raise CskError(rc, "csk_solve_host")
     rec = info[0]
     return x_out, {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}, rc
+
+
+def csk_sketch_noalloc(A: torch.Tensor, d: int, seed: int, b: torch.Tensor | None = None, *,
+                       norms: bool = True, perm: bool = False, off: bool = False) -> Sketch:
+    """csk_sketch through the entry point that takes no workspace: the
+    library's static scratch is used instead (m <= 2^20, d <= 2^18; calls
+    must not overlap on the GPU).  Outputs are allocated here as usual."""
+    dev = _check_cuda(A, b)
+    lda = _rowmajor(A)
+    m, n = A.shape
+    dt = _dtype_code(A)
+    nrhs, ldb, B = 0, 0, None
+    if b is not None:
+        if b.dtype != A.dtype:
+            raise TypeError("b must have A's dtype")
+        B = b.reshape(m, -1)
+        if B.stride(1) != 1:
+            raise ValueError("b must be contiguous along right-hand sides")
+        nrhs, ldb = B.shape[1], B.stride(0)
+    At = torch.empty((d, n), dtype=A.dtype, device=dev)
+    bt = torch.empty((d, nrhs), dtype=A.dtype, device=dev) if nrhs else None
+    N2 = torch.empty(d, dtype=torch.float64, device=dev) if norms else None
+    P = torch.empty(m, dtype=torch.int32, device=dev) if perm else None
+    O = torch.empty(d + 1, dtype=torch.int32, device=dev) if off else None
+    rc = lib().csk_sketch_noalloc(_ptr(A), m, n, lda, _ptr(B), ldb, nrhs, dt, d,
+                                  seed & (2**64 - 1), _ptr(At), _ptr(bt), _ptr(N2), _ptr(P),
+                                  _ptr(O), _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_sketch_noalloc")
+    if bt is not None and b.dim() == 1:
+        bt = bt[:, 0]
+    return Sketch(At, bt, N2, P, O)
