@@ -35,9 +35,8 @@ __global__ void k_info_init(csk_info* info, int path, int rows, int grid) {
 
 // Workspace of csk_solve, in order (each piece 256-byte aligned):
 //   sort scratch | At (d x n) | bt (d) | N2 (rows) | stop norm (8 doubles) |
-//   slots (2 x kMaxSlots) | x gather (n) | final-check partials |
+//   exchange mailboxes (2 x grid x grid) | x gather (n) | final-check partials |
 //   G (d x d, GRAM) | Gram operand scratch (GRAM)
-constexpr int kMaxSlots = 1024;
 
 struct SolveLayout {
     size_t sort, At, bt, N2, norm, slots, xg, part, G, gscr, total;
@@ -52,7 +51,7 @@ void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLay
     L->bt = o;    o += d > 0 ? align256((size_t)d * s) : 0;
     L->N2 = o;    o += align256((size_t)rows * 8);
     L->norm = o;  o += 256;
-    L->slots = o; o += align256((size_t)2 * kMaxSlots * sizeof(Slot));
+    L->slots = o; o += align256(exchange_bytes(kMaxIterGrid));
     L->xg = o;    o += align256((size_t)n * s);
     L->part = o;  o += align256(final_check_partials((int)rows) * 8);
     L->G = o;     o += path == CSK_RESID_GRAM ? align256((size_t)rows * gram_ld((int)rows) * 4) : 0;
@@ -122,7 +121,7 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     IterConfig cfg;
     int rc = plan_iterate(path, dtype, rows, (int)n, params->grid, &cfg);
     if (rc != CSK_OK) return rc;
-    if (cfg.grid > kMaxSlots) return CSK_EUNSUPPORTED;
+    if (cfg.grid > kMaxIterGrid) return CSK_EUNSUPPORTED;
 
     char* w = static_cast<char*>(ws);
     const void* At;
@@ -153,7 +152,7 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     if (launch_norm2(dtype, x_star ? x_star : bt, x_star ? n : rows, stop_norm, st) != cudaSuccess)
         return CSK_ECUDA;
     Slot* slots = reinterpret_cast<Slot*>(w + L.slots);
-    if (cudaMemsetAsync(slots, 0, (size_t)2 * cfg.grid * sizeof(Slot), st) != cudaSuccess)
+    if (cudaMemsetAsync(slots, 0, exchange_bytes(cfg.grid), st) != cudaSuccess)
         return CSK_ECUDA;
     float* G = nullptr;
     if (path == CSK_RESID_GRAM) {

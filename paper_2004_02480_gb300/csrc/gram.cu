@@ -242,23 +242,36 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             uint32_t v[32];
             tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             const int col0 = bj * BN + c0;
-            if (row < d) {
-                float* dst = G + (int64_t)row * ldg + col0;
-                if (vec_ok && col0 + 32 <= d) {
-#pragma unroll
-                    for (int q = 0; q < 32; q += 4)
-                        *reinterpret_cast<float4*>(dst + q) =
-                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
-                                        __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
-                } else {
-                    for (int q = 0; q < 32 && col0 + q < d; ++q) dst[q] = __uint_as_float(v[q]);
-                }
-            }
             if (bj != bi) {
+                if (row < d) {
+                    float* dst = G + (int64_t)row * ldg + col0;
+                    if (vec_ok && col0 + 32 <= d) {
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4)
+                            *reinterpret_cast<float4*>(dst + q) =
+                                make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                            __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (col0 + q < d) dst[q] = __uint_as_float(v[q]);
+                    }
+                }
                 // mirrored tile: G[col][row] -- consecutive lanes, consecutive addresses
 #pragma unroll
                 for (int q = 0; q < 32; ++q)
                     if (col0 + q < d && row < d) G[(int64_t)(col0 + q) * ldg + row] = __uint_as_float(v[q]);
+            } else {
+                // diagonal tile: (r, c) and (c, r) are summed in different
+                // orders here, so keep the upper triangle and mirror it
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int col = col0 + q;
+                    if (row < d && col < d && col >= row) {
+                        G[(int64_t)row * ldg + col] = __uint_as_float(v[q]);
+                        G[(int64_t)col * ldg + row] = __uint_as_float(v[q]);
+                    }
+                }
             }
         }
     } else if (threadIdx.x == 0 && info) {

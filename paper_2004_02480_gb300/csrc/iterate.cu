@@ -38,9 +38,8 @@ namespace {
 
 constexpr int kIterThreads = 256;
 constexpr int kWarps = kIterThreads / 32;
-constexpr int kMaxGrid = 1024;
 constexpr int64_t kDefaultSpin = 1ll << 22;
-constexpr int kRowsPerWarp = 4;          // rows a warp scores together (ILP)
+constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP)
 
 // ----------------------------------------------------- candidate algebra
 // Larger key wins; equal keys -> smaller row (first maximiser); NaN keys win
@@ -93,14 +92,36 @@ __device__ __forceinline__ Red<T> block_reduce(Red<T> c, RedShared<T>& sh, int& 
     return r;
 }
 
-// ---------------------------------------------------------- exchanges
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+// The same, for partials whose candidate is already uniform across each warp
+// (Phase A: every lane of a warp holds the row results of that warp), so only
+// the statistic needs a warp sum before the cross-warp step.
+template <typename T>
+__device__ __forceinline__ Red<T> block_reduce_wu(Red<T> c, RedShared<T>& sh, int& par) {
+    c.stat = warp_sum(c.stat);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.buf[par][warp] = c;
+    __syncthreads();
+    Red<T> r;
+    if (lane < kWarps) r = sh.buf[par][lane];
+    else { r.key = T(-1); r.alpha = T(0); r.stat = T(0); r.idx = INT_MAX; }
+    par ^= 1;
+    warp_reduce(r);
+    return r;
 }
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
+
+// ---------------------------------------------------------- exchanges
+// Mailboxes: bank (round parity) x destination CTA x source CTA, 32 bytes
+// each.  A CTA writes its candidate into every destination's mailbox and
+// polls only its own, so no cache line is polled by more than one CTA.
+__device__ __forceinline__ void st_relaxed_v2(uint64_t* p, uint64_t a, uint64_t b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const uint64_t* p, uint64_t& a, uint64_t& b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ Slot* mailbox(Slot* slots, uint32_t round, int dest, int src) {
+    const int G = gridDim.x;
+    return slots + ((size_t)(round & 1u) * G + dest) * G + src;
 }
 
 // FP32: four stamped words per slot.
@@ -110,27 +131,23 @@ __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>
                                          int64_t spin_limit, int fault_inject, csk_info* info,
                                          RedShared<float>& sh, int& par, bool acquire = false) {
     const int G = gridDim.x, b = blockIdx.x;
-    uint64_t* bank = reinterpret_cast<uint64_t*>(slots + (size_t)(round & 1u) * G);
     const uint64_t stamp = (uint64_t)(round + 1u) << 32;
-    if (threadIdx.x == 0 && !(fault_inject && b == 0)) {
-        uint64_t* w = bank + 4 * b;
-        st_relaxed_u64(w + 0, stamp | __float_as_uint(c.key));
-        st_relaxed_u64(w + 1, stamp | __float_as_uint(c.alpha));
-        st_relaxed_u64(w + 2, stamp | __float_as_uint(c.stat));
-        st_relaxed_u64(w + 3, stamp | (uint32_t)c.idx);
-    }
+    if (!(fault_inject && b == 0))
+        for (int t = threadIdx.x; t < G; t += blockDim.x) {
+            uint64_t* w = reinterpret_cast<uint64_t*>(mailbox(slots, round, t, b));
+            st_relaxed_v2(w, stamp | __float_as_uint(c.key), stamp | __float_as_uint(c.alpha));
+            st_relaxed_v2(w + 2, stamp | __float_as_uint(c.stat), stamp | (uint32_t)c.idx);
+        }
     Red<float> g;
     g.key = -1.0f; g.alpha = 0.0f; g.stat = 0.0f; g.idx = INT_MAX;
     int timed_out = 0;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
-        const uint64_t* w = bank + 4 * t;
+        const uint64_t* w = reinterpret_cast<const uint64_t*>(mailbox(slots, round, b, t));
         uint64_t v0, v1, v2, v3;
         int64_t spins = 0;
         for (;;) {
-            v0 = ld_relaxed_u64(w + 0);
-            v1 = ld_relaxed_u64(w + 1);
-            v2 = ld_relaxed_u64(w + 2);
-            v3 = ld_relaxed_u64(w + 3);
+            ld_relaxed_v2(w, v0, v1);
+            ld_relaxed_v2(w + 2, v2, v3);
             const uint64_t hi = stamp >> 32;
             if ((v0 >> 32) == hi && (v1 >> 32) == hi && (v2 >> 32) == hi && (v3 >> 32) == hi) break;
             if (++spins > spin_limit) { timed_out = 1; break; }
@@ -155,27 +172,29 @@ __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<double
                                          int64_t spin_limit, int fault_inject, csk_info* info,
                                          RedShared<double>& sh, int& par) {
     const int G = gridDim.x, b = blockIdx.x;
-    Slot* bank = slots + (size_t)(round & 1u) * G;
-    if (threadIdx.x == 0 && !(fault_inject && b == 0)) {
-        bank[b].key = c.key;
-        bank[b].alpha = c.alpha;
-        bank[b].stat = c.stat;
-        bank[b].idx = c.idx;
-        st_release_u32(&bank[b].stamp, round + 1u);
-    }
+    if (!(fault_inject && b == 0))
+        for (int t = threadIdx.x; t < G; t += blockDim.x) {
+            Slot* w = mailbox(slots, round, t, b);
+            w->key = c.key;
+            w->alpha = c.alpha;
+            w->stat = c.stat;
+            w->idx = c.idx;
+            st_release_u32(&w->stamp, round + 1u);
+        }
     Red<double> g;
     g.key = -1.0; g.alpha = 0.0; g.stat = 0.0; g.idx = INT_MAX;
     int timed_out = 0;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        Slot* w = mailbox(slots, round, b, t);
         int64_t spins = 0;
-        while (ld_acquire_u32(&bank[t].stamp) != round + 1u) {
+        while (ld_acquire_u32(&w->stamp) != round + 1u) {
             if (++spins > spin_limit) { timed_out = 1; break; }
         }
         if (timed_out) break;
-        const double k2 = __ldcg(&bank[t].key);
-        const int32_t i2 = __ldcg(&bank[t].idx);
-        g.stat += __ldcg(&bank[t].stat);
-        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = __ldcg(&bank[t].alpha); g.idx = i2; }
+        const double k2 = __ldcg(&w->key);
+        const int32_t i2 = __ldcg(&w->idx);
+        g.stat += __ldcg(&w->stat);
+        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = __ldcg(&w->alpha); g.idx = i2; }
     }
     if (__syncthreads_or(timed_out)) {
         if (threadIdx.x == 0) set_status_once(info, CSK_ETIMEOUT);
@@ -252,32 +271,51 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     const int64_t lda = cache_rows ? (int64_t)n : p.ld;
     const T* Abase = cache_rows ? As : At + (int64_t)r0 * p.ld;
+    // 128-bit row loads: FP32, n % 4 == 0 and 16-byte aligned rows
+    const bool vec4 = sizeof(T) == 4 && (n & 3) == 0 && (lda & 3) == 0 &&
+                      (reinterpret_cast<uintptr_t>(Abase) & 15) == 0;
     uint32_t round = 0;
     int64_t k = 0;
     int status = CSK_OK;
     for (;;) {
-        // Phase A: residuals of the owned rows, kRowsPerWarp rows at a time
+        // Phase A: residuals of the owned rows.  Warp w scores rows
+        // w, w + kWarps, ... (round robin), up to kRowsPerWarp in one pass
+        // over the columns so their loads overlap.
         Red<T> c;
         c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
-        for (int q0 = warp * kRowsPerWarp; q0 < nr; q0 += kWarps * kRowsPerWarp) {
+        for (int base = warp; base < nr; base += kWarps * kRowsPerWarp) {
+            const int myrows = min(kRowsPerWarp, (nr - base + kWarps - 1) / kWarps);
             T acc[kRowsPerWarp];
-            const T* a[kRowsPerWarp];
+#pragma unroll
+            for (int u = 0; u < kRowsPerWarp; ++u) acc[u] = T(0);
+            if (vec4) {
+                const float4* x4 = reinterpret_cast<const float4*>(xs);
+                for (int c4 = lane; c4 < (n >> 2); c4 += 32) {
+                    const float4 xv = x4[c4];
+#pragma unroll
+                    for (int u = 0; u < kRowsPerWarp; ++u)
+                        if (u < myrows) {
+                            const float4 a = reinterpret_cast<const float4*>(
+                                Abase + (int64_t)(base + u * kWarps) * lda)[c4];
+                            acc[u] = fma((T)a.x, (T)xv.x, acc[u]);
+                            acc[u] = fma((T)a.y, (T)xv.y, acc[u]);
+                            acc[u] = fma((T)a.z, (T)xv.z, acc[u]);
+                            acc[u] = fma((T)a.w, (T)xv.w, acc[u]);
+                        }
+                }
+            } else {
+                for (int col = lane; col < n; col += 32) {
+                    const T xv = xs[col];
+#pragma unroll
+                    for (int u = 0; u < kRowsPerWarp; ++u)
+                        if (u < myrows) acc[u] = fma(Abase[(int64_t)(base + u * kWarps) * lda + col], xv, acc[u]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kRowsPerWarp; ++u) {
-                acc[u] = T(0);
-                a[u] = Abase + (int64_t)min(q0 + u, nr - 1) * lda;
-            }
-            for (int col = lane; col < n; col += 32) {
-                const T xv = xs[col];
-#pragma unroll
-                for (int u = 0; u < kRowsPerWarp; ++u) acc[u] = fma(a[u][col], xv, acc[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < kRowsPerWarp; ++u) {
-                const T dot = warp_sum(acc[u]);
-                const int q = q0 + u;
-                if (q < nr) {
-                    const T r = bts[q] - dot;
+                if (u < myrows) {
+                    const int q = base + u * kWarps;
+                    const T r = bts[q] - warp_sum(acc[u]);
                     const T w = w2s[q];
                     if (!(w < T(0))) {
                         const T key = r * r * w;
@@ -292,7 +330,7 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 const T t = xs[col] - xss[col - c0];
                 c.stat += t * t;
             }
-        c = block_reduce(c, sh, par);
+        c = block_reduce_wu(c, sh, par);
         // Phase B
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
@@ -514,7 +552,7 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cf
     const int s = dtype == CSK_F64 ? 8 : 4;
     const size_t budget = (size_t)di.smem_optin - 2048;   // static shared + slack
     int G = grid_req > 0 ? grid_req : di.sms;
-    if (G > kMaxGrid) G = kMaxGrid;
+    if (G > kMaxIterGrid) G = kMaxIterGrid;
     if (G > d) G = d;
     if (G < 1) G = 1;
     if (grid_req <= 0) {

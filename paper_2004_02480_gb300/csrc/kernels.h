@@ -52,6 +52,10 @@ cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int
 cudaError_t launch_norm2(int dtype, const void* v, int64_t len, double* out, cudaStream_t st);
 
 // -------------------------------------------------------------- iterate
+// Largest CTA count of the persistent loop; the exchange mailboxes take
+// 2 * grid * grid * sizeof(Slot) bytes.
+constexpr int kMaxIterGrid = 320;
+inline size_t exchange_bytes(int grid) { return (size_t)2 * grid * grid * 32; }
 struct IterConfig {
     int grid = 0;           // CTAs
     int threads = 256;

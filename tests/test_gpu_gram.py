@@ -3,12 +3,16 @@ path of the iteration.
 
 Tolerances (derived, not tuned):
 * GPU G against the oracle's split product (the same BF16 operands, summed
-  exactly in binary64): the only difference is FP32 accumulation of K = 3n
-  products; with random signs its error is ~ K u |term| = 3 u (|A||A|^T)_ij
-  (u = 2^-24), so |G - G_split| <= 2^-17 (|A||A|^T)_ij leaves an 8x margin,
-  while a dropped hi*lo term would be ~2^-9 / sqrt(n) of (|A||A|^T)_ij.
-* GPU G against the exact product: the split drops lo*lo and rounds lo,
-  2^-16 relative per product, so |G - A A^T| <= 2^-14 (|A||A|^T)_ij.
+  exactly in binary64): the difference is the tensor core's FP32
+  accumulation.  Measured on GB300 it rounds toward zero once per
+  K = 16 instruction (every GPU value lies on the zero side of the exact
+  split sum), so over M = 3 * k_pad / 16 instructions
+  |G - G_split| <= (M + 16) 2^-23 (|A||A|^T)_ij, where k_pad = 64 ceil(n/64).
+  An RMS check adds sensitivity: a dropped hi*lo segment would leave a
+  relative RMS error near 2^-9, the accumulation about 1e-5 or less.
+* GPU G against the exact product: the split drops lo*lo and rounds lo
+  (2^-16 relative per product) on top of the accumulation above, so
+  |G - A A^T| <= (2^-14 + (M + 16) 2^-23) (|A||A|^T)_ij.
 * G is exactly symmetric and G_jj = fl32(||A_j||^2).
 """
 import numpy as np
@@ -31,15 +35,20 @@ def csk():
 
 def _check_G(G, At, rows=None, Gs_rows=None):
     A64 = At.astype(np.float64)
-    rows = np.arange(At.shape[0]) if rows is None else np.asarray(rows)
+    d, n = At.shape
+    rows = np.arange(d) if rows is None else np.asarray(rows)
     Gs = oracle.gram_split_bf16(At) if Gs_rows is None else Gs_rows
     if Gs_rows is None:
         Gs = Gs[rows]
     scale = np.abs(A64[rows]) @ np.abs(A64).T
     exact = A64[rows] @ A64.T
     Gr = G[rows].astype(np.float64)
-    assert np.all(np.abs(Gr - Gs) <= 2.0 ** -17 * scale)
-    assert np.all(np.abs(Gr - exact) <= 2.0 ** -14 * scale)
+    M = 3 * ((n + 63) // 64 * 64) // 16
+    acc = (M + 16) * 2.0 ** -23
+    assert np.all(np.abs(Gr - Gs) <= acc * scale)
+    assert np.all(np.abs(Gr - exact) <= (2.0 ** -14 + acc) * scale)
+    rms = np.sqrt(np.mean((Gr - Gs) ** 2) / max(np.mean(Gs ** 2), 1e-300))
+    assert rms <= 3e-5, rms
 
 
 @pytest.mark.parametrize("d,n", [(1, 1), (5, 3), (300, 70), (1000, 256), (129, 65), (777, 1000)])
