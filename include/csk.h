@@ -84,6 +84,8 @@ typedef struct {
                                step k < x_log_len, row k of an x_log_len x n
                                array -- the iterate step k selects from          */
     int64_t x_log_len;
+    int32_t threads;        /* csk_solve_batched: threads per CTA, 0 = choice    */
+    int32_t reserved_;
     void *stage_events[5];  /* optional cudaEvent_t handles (caller-owned), each
                                recorded on the stream when non-NULL: [0] before
                                the sketch, [1] after sketch and row norms, [2]
@@ -234,6 +236,46 @@ int csk_solve_host(const void *A_host, int64_t m, int64_t n, int64_t lda,
                    const void *x0_host, const void *x_star_host,
                    void *x_out_host, csk_info *info_host,
                    void *ws, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------------
+ * csk_solve_batched -- many independent systems, each with several
+ * right-hand sides, in one persistent launch (FP32, GRAM residual path).
+ *
+ * Each (system, right-hand side) pair is one run of Algorithm 1 with the
+ * system's own count sketch (d, seed) and the Section 3 stopping rule; the
+ * sketch and split-BF16 Gram matrix of a system are formed once and shared
+ * by its right-hand sides.  A CTA runs one pair at a time to completion,
+ * pairs ordered by decreasing d*n; CTAs never wait for each other.
+ * Every array in csk_system is device memory; B, X0, Xstar and Xout hold one
+ * column per right-hand side (row-major, leading dimensions ldb / nrhs).
+ * info: nrhs csk_info records per system (device), written when the pair
+ * finishes; rse is FP64, resid uses a compensated FP32 dot product.
+ * params: tol, max_iter, refresh_every (FP64 residual recomputation period,
+ * 0 = never), grid and threads (0 = library choice); d/seed/path ignored.
+ * The host array `sys` is read during the call only, and nothing in the call
+ * synchronises, so the sequence can be captured in a CUDA graph.
+ * ws: csk_solve_batched_workspace_size(sys, nsys) bytes (sketches, Gram
+ * matrices and descriptors of every system).
+ * -------------------------------------------------------------------- */
+typedef struct {
+    const void *A;        /* m x n FP32, leading dimension lda                  */
+    int64_t m, n, lda;
+    const void *B;        /* m x nrhs FP32, leading dimension ldb               */
+    int64_t ldb;
+    int32_t nrhs;
+    int32_t reserved_;
+    int64_t d;            /* sketch rows of this system                         */
+    uint64_t seed;        /* sketch seed of this system                         */
+    const void *X0;       /* nullable, n x nrhs                                 */
+    const void *Xstar;    /* nullable, n x nrhs                                 */
+    void *Xout;           /* n x nrhs                                           */
+    csk_info *info;       /* nrhs records                                       */
+} csk_system;
+
+size_t csk_solve_batched_workspace_size(const csk_system *sys, int32_t nsys);
+
+int csk_solve_batched(const csk_system *sys, int32_t nsys, const csk_params *params,
+                      void *ws, size_t ws_bytes, void *stream);
 
 #ifdef __cplusplus
 }

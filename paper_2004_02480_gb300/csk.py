@@ -44,7 +44,16 @@ class csk_params(ctypes.Structure):
                 ("ik_log", ctypes.c_void_p), ("ik_log_len", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("x_log", ctypes.c_void_p), ("x_log_len", ctypes.c_int64),
+                ("threads", ctypes.c_int32), ("reserved_", ctypes.c_int32),
                 ("stage_events", ctypes.c_void_p * 5)]
+
+
+class csk_system(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("nrhs", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("d", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("X0", ctypes.c_void_p), ("Xstar", ctypes.c_void_p),
+                ("Xout", ctypes.c_void_p), ("info", ctypes.c_void_p)]
 
 
 INFO_DTYPE = np.dtype([("status", "<i4"), ("path", "<i4"), ("iters", "<i8"), ("rse", "<f8"),
@@ -80,6 +89,11 @@ def lib():
                                 P, sz, P]
         L.csk_solve.restype = ctypes.c_int
         L.csk_kernel_launches.restype = ctypes.c_int64
+        L.csk_solve_batched_workspace_size.argtypes = [ctypes.POINTER(csk_system), i32]
+        L.csk_solve_batched_workspace_size.restype = sz
+        L.csk_solve_batched.argtypes = [ctypes.POINTER(csk_system), i32,
+                                        ctypes.POINTER(csk_params), P, sz, P]
+        L.csk_solve_batched.restype = ctypes.c_int
         L.csk_gram_workspace_size.argtypes = [i64, i64]
         L.csk_gram_workspace_size.restype = sz
         L.csk_gram.argtypes = [P, i64, i64, P, P, i64, P, P, sz, P]
@@ -349,3 +363,65 @@ def csk_sketch_noalloc(A: torch.Tensor, d: int, seed: int, b: torch.Tensor | Non
     if bt is not None and b.dim() == 1:
         bt = bt[:, 0]
     return Sketch(At, bt, N2, P, O)
+
+
+@dataclass
+class BatchSystem:
+    """One system of a batched solve (device tensors)."""
+    A: torch.Tensor               # m x n FP32
+    B: torch.Tensor               # m x R FP32
+    d: int
+    seed: int
+    X0: torch.Tensor | None = None      # n x R
+    Xstar: torch.Tensor | None = None   # n x R
+    Xout: torch.Tensor | None = None    # n x R (allocated when None)
+    info: torch.Tensor | None = None    # R x 64 bytes (allocated when None)
+
+
+def _systems(batch: list[BatchSystem]):
+    arr = (csk_system * len(batch))()
+    for i, y in enumerate(batch):
+        _check_cuda(y.A, y.B, y.X0, y.Xstar, y.Xout, y.info)
+        if y.A.dtype != torch.float32 or y.B.dtype != torch.float32:
+            raise TypeError("batched solves take FP32 systems")
+        m, n = y.A.shape
+        R = y.B.shape[1]
+        for t in (y.X0, y.Xstar):
+            if t is not None and (tuple(t.shape) != (n, R) or not t.is_contiguous()):
+                raise ValueError("X0 / Xstar must be contiguous n x R")
+        if y.Xout is None:
+            y.Xout = torch.empty((n, R), dtype=torch.float32, device=y.A.device)
+        if y.info is None:
+            y.info = torch.zeros((R, 64), dtype=torch.uint8, device=y.A.device)
+        arr[i] = csk_system(_ptr(y.A), m, n, _rowmajor(y.A), _ptr(y.B), y.B.stride(0), R, 0, y.d,
+                            y.seed & (2**64 - 1), _ptr(y.X0), _ptr(y.Xstar), _ptr(y.Xout),
+                            _ptr(y.info))
+    return arr
+
+
+def csk_solve_batched_workspace_size(batch: list[BatchSystem]) -> int:
+    arr = _systems(batch)
+    return int(lib().csk_solve_batched_workspace_size(arr, len(batch)))
+
+
+def csk_solve_batched(batch: list[BatchSystem], params: csk_params, *, ws: torch.Tensor | None = None,
+                      sync: bool = True):
+    """All (system, right-hand side) solves of ``batch`` in one persistent launch.
+    Returns per-system (Xout, list of info dicts) when ``sync``."""
+    arr = _systems(batch)
+    dev = batch[0].A.device
+    if ws is None:
+        ws = _workspace(int(lib().csk_solve_batched_workspace_size(arr, len(batch))), dev)
+    rc = lib().csk_solve_batched(arr, len(batch), ctypes.byref(params), _ptr(ws), ws.numel(),
+                                 _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_solve_batched")
+    if not sync:
+        return batch
+    torch.cuda.synchronize(dev)
+    out = []
+    for y in batch:
+        recs = np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=INFO_DTYPE)
+        out.append((y.Xout, [{k: r[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}
+                             for r in recs]))
+    return out

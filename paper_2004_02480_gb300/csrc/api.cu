@@ -4,7 +4,9 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -63,6 +65,11 @@ int check_stream_device(cudaStream_t st) {
     int cur = 0;
     if (cudaGetDevice(&cur) != cudaSuccess) return CSK_ECUDA;
     if (st == nullptr) return CSK_OK;
+    // A stream being captured into a CUDA graph cannot be queried for its
+    // device (the query would invalidate the capture); skip the check then.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return CSK_EINVAL;
+    if (cap != cudaStreamCaptureStatusNone) return CSK_OK;
     int sd = -1;
     if (cudaStreamGetDevice(st, &sd) != cudaSuccess) return CSK_EINVAL;
     return sd == cur ? CSK_OK : CSK_EINVAL;
@@ -189,6 +196,38 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
 
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_set;                  // largest set so far
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occupancy;
+}  // namespace
+
+cudaError_t ensure_smem_attr(const void* fn, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto key = std::make_pair(dev, fn);
+    auto it = g_smem_set.find(key);
+    if (it != g_smem_set.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) g_smem_set[key] = smem;
+    return e;
+}
+
+cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto key = std::make_tuple(dev, fn, threads, smem);
+    auto it = g_occupancy.find(key);
+    if (it != g_occupancy.end()) { *per_sm = it->second; return cudaSuccess; }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
+    if (e == cudaSuccess) g_occupancy[key] = *per_sm;
+    return e;
+}
+
 int dev_info(DevInfo* out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
@@ -283,6 +322,23 @@ int csk_gram(const float* At, int64_t d, int64_t n, const double* norms2, float*
     if (launch_gram_split_bf16(At, (int)d, (int)n, norms2, G, ldg, ws, info, st) != cudaSuccess)
         return CSK_ECUDA;
     return CSK_OK;
+}
+
+size_t csk_solve_batched_workspace_size(const csk_system* sys, int32_t nsys) {
+    return batched_workspace_bytes(sys, nsys);
+}
+
+int csk_solve_batched(const csk_system* sys, int32_t nsys, const csk_params* params, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!sys || nsys < 1 || !params || !ws) return CSK_EINVAL;
+    if (!(params->tol >= 0.0) || params->max_iter < 0 || params->refresh_every < 0 ||
+        params->grid < 0 || params->threads < 0)
+        return CSK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    return launch_batched(sys, nsys, params, ws, ws_bytes, st);
 }
 
 size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_params* params) {

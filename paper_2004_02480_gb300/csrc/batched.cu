@@ -1,0 +1,407 @@
+// batched.cu -- many independent CSK solves (systems of uneven m, n, d, each
+// with many right-hand sides) in one persistent launch.
+//
+// Per system s the stream carries its sketch (At_s = S_s A_s, Bt_s = S_s B_s,
+// FP64 row norms) and its split-BF16 Gram matrix G_s = At_s At_s^T (the same
+// kernels as csk_sketch / csk_gram).  Then one persistent kernel runs every
+// (system, right-hand side) pair -- a "unit" -- to completion: a CTA takes the
+// next unit from an atomic counter (units are ordered by decreasing d*n so the
+// long solves start first) and runs the whole MWRK loop of Algorithm 1 on it
+// alone, with r, the row weights and x in its shared memory and the GRAM
+// residual update r -= alpha G_s[i_k, :] (r_{i_k} = 0 exactly).  A step costs
+// one pass over the CTA's rows and one CTA barrier; no CTA waits for another.
+// The final check (FP64 RES; ||bt - At x|| / ||bt|| with a compensated FP32
+// dot product, GB300's FP64 rate being a small fraction of FP32) is done by
+// the same CTA.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace csk {
+
+namespace {
+
+struct BatchSys {
+    const float* At;
+    const float* Bt;
+    const double* N2;
+    const float* G;
+    const float* X0;
+    const float* Xstar;
+    float* Xout;
+    csk_info* info;
+    int64_t ldg;
+    int32_t d, n, nrhs, unit_begin;
+};
+
+constexpr int kTableChunk = 32;   // descriptors per table-writing launch (params < 4 KB)
+
+struct TableChunk {
+    BatchSys e[kTableChunk];
+    int count, first;
+};
+
+__global__ void k_write_table(TableChunk c, BatchSys* table) {
+    const int i = threadIdx.x;
+    if (i < c.count) table[c.first + i] = c.e[i];
+}
+
+template <typename T>
+struct Red {
+    T key, alpha, stat;
+    int32_t idx;
+};
+
+__device__ __forceinline__ bool better(float ka, int32_t ia, float kb, int32_t ib) {
+    const bool na = ka != ka, nb = kb != kb;
+    if (na != nb) return na;
+    if (na) return ia < ib;
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+__device__ __forceinline__ void warp_reduce(Red<float>& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float k2 = __shfl_xor_sync(0xffffffffu, c.key, o);
+        const float a2 = __shfl_xor_sync(0xffffffffu, c.alpha, o);
+        const int32_t i2 = __shfl_xor_sync(0xffffffffu, c.idx, o);
+        c.stat += __shfl_xor_sync(0xffffffffu, c.stat, o);
+        if (better(k2, i2, c.key, c.idx)) { c.key = k2; c.alpha = a2; c.idx = i2; }
+    }
+}
+
+constexpr int kMaxWarps = 32;
+
+struct BatchShared {
+    Red<float> buf[2][kMaxWarps];
+    double dbuf[kMaxWarps];
+    int unit;
+};
+
+__device__ __forceinline__ Red<float> block_reduce(Red<float> c, BatchShared& sh, int& par) {
+    warp_reduce(c);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lane == 0) sh.buf[par][warp] = c;
+    __syncthreads();
+    Red<float> r;
+    if (lane < nw) r = sh.buf[par][lane];
+    else { r.key = -1.0f; r.alpha = 0.0f; r.stat = 0.0f; r.idx = INT_MAX; }
+    par ^= 1;
+    warp_reduce(r);
+    return r;
+}
+
+__device__ __forceinline__ double block_sum_f64(double v, BatchShared& sh) {
+    v = warp_sum(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.dbuf[warp] = v;
+    __syncthreads();
+    double s = lane < nw ? sh.dbuf[lane] : 0.0;
+    return warp_sum(s);
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + t == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+    s = a + b;
+    const float bb = s - a;
+    t = (a - (s - bb)) + (b - bb);
+}
+
+__device__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
+                           int64_t max_iter, int refresh) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
+              nw = nt >> 5;
+    const int d = S.d, n = S.n, R = S.nrhs;
+    const int dpad = (d + 3) & ~3, npad = (n + 3) & ~3;
+    float* rs = sm;
+    float* w2s = rs + dpad;
+    float* xs = w2s + dpad;
+    float* xss = xs + npad;
+    int par = 0;
+
+    for (int j = tid; j < d; j += nt) {
+        rs[j] = S.Bt[(int64_t)j * R + rhs];
+        const double N = S.N2[j];
+        w2s[j] = N > 0.0 ? (float)(1.0 / N) : (N == 0.0 ? -1.0f : NAN);
+    }
+    for (int c = tid; c < n; c += nt) {
+        xs[c] = S.X0 ? S.X0[(int64_t)c * R + rhs] : 0.0f;
+        xss[c] = S.Xstar ? S.Xstar[(int64_t)c * R + rhs] : 0.0f;
+    }
+    __syncthreads();
+    // stopping threshold tol * ||x*||^2 (or tol * ||bt||^2 without x*)
+    double nrm = 0.0;
+    if (S.Xstar) for (int c = tid; c < n; c += nt) nrm += (double)xss[c] * (double)xss[c];
+    else for (int j = tid; j < d; j += nt) nrm += (double)rs[j] * (double)rs[j];
+    nrm = block_sum_f64(nrm, sh);
+    const float threshold = (float)(tol * nrm);
+    const bool fresh_r = (S.X0 != nullptr);
+    int64_t k = 0;
+    int status = CSK_OK;
+    int32_t idx = -1;
+    float alpha = 0.0f;
+    for (;;) {
+        if (k == 0 ? fresh_r : (refresh > 0 && k % refresh == 0)) {
+            // r = bt - At x with FP64 accumulation (x0 given, or periodic refresh)
+            if (idx >= 0) {
+                const float* arow = S.At + (int64_t)idx * n;
+                for (int c = tid; c < n; c += nt) xs[c] = fmaf(alpha, arow[c], xs[c]);
+                idx = -1;
+            }
+            __syncthreads();
+            for (int j = warp; j < d; j += nw) {
+                const float* a = S.At + (int64_t)j * n;
+                double acc = 0.0;
+                for (int c = lane; c < n; c += 32) acc = fma((double)a[c], (double)xs[c], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) rs[j] = (float)((double)S.Bt[(int64_t)j * R + rhs] - acc);
+            }
+            __syncthreads();
+        }
+        // one pass: apply the previous step's update, then score
+        Red<float> c;
+        c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
+        const float* grow = idx >= 0 ? S.G + (int64_t)idx * S.ldg : nullptr;
+        for (int j = tid; j < d; j += nt) {
+            float r = rs[j];
+            if (grow) {
+                r = (j == idx) ? 0.0f : fmaf(-alpha, __ldg(grow + j), r);
+                rs[j] = r;
+            }
+            const float w = w2s[j];
+            if (!(w < 0.0f)) {
+                const float key = r * r * w;
+                if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = j; }
+            }
+            if (!S.Xstar) c.stat += r * r;
+        }
+        const float* arow = idx >= 0 ? S.At + (int64_t)idx * n : nullptr;
+        for (int col = tid; col < n; col += nt) {
+            float x = xs[col];
+            if (arow) {
+                x = fmaf(alpha, __ldg(arow + col), x);
+                xs[col] = x;
+            }
+            if (S.Xstar) {
+                const float t = x - xss[col];
+                c.stat += t * t;
+            }
+        }
+        c = block_reduce(c, sh, par);
+        if (c.stat <= threshold) { status = CSK_OK; break; }
+        if (k >= max_iter) { status = CSK_MAXITER; break; }
+        if (c.key != c.key || c.key < 0.0f) { status = CSK_ENUMERIC; break; }
+        if (c.key == 0.0f) { status = CSK_OK; break; }
+        idx = c.idx;
+        alpha = c.alpha;
+        ++k;
+    }
+    __syncthreads();
+    // outputs and final check
+    for (int col = tid; col < n; col += nt) S.Xout[(int64_t)col * R + rhs] = xs[col];
+    double ee = 0.0, ss = 0.0;
+    if (S.Xstar)
+        for (int col = tid; col < n; col += nt) {
+            const double e = (double)xs[col] - (double)xss[col];
+            ee += e * e;
+            ss += (double)xss[col] * (double)xss[col];
+        }
+    double rr = 0.0, bb = 0.0, empty = 0.0;
+    for (int j = tid; j < d; j += nt) empty += (w2s[j] < 0.0f) ? 1.0 : 0.0;
+    for (int j = warp; j < d; j += nw) {
+        const float* a = S.At + (int64_t)j * n;
+        float hi = 0.0f, lo = 0.0f;
+        for (int col = lane; col < n; col += 32) {
+            const float p = a[col] * xs[col];
+            const float e = fmaf(a[col], xs[col], -p);
+            float s, t;
+            two_sum(hi, p, s, t);
+            hi = s;
+            lo += t + e;
+        }
+        double dot = (double)hi + (double)lo;
+        dot = warp_sum(dot);
+        if (lane == 0) {
+            const double bj = (double)S.Bt[(int64_t)j * R + rhs];
+            const double r = bj - dot;
+            rr += r * r;
+            bb += bj * bj;
+        }
+    }
+    ee = block_sum_f64(ee, sh);
+    ss = block_sum_f64(ss, sh);
+    rr = block_sum_f64(rr, sh);
+    bb = block_sum_f64(bb, sh);
+    empty = block_sum_f64(empty, sh);
+    if (tid == 0) {
+        csk_info* info = S.info + rhs;
+        info->status = status;
+        info->path = CSK_RESID_GRAM;
+        info->iters = k;
+        info->rse = S.Xstar ? ee / ss : (double)NAN;
+        info->resid = sqrt(rr / bb);
+        info->rows = d;
+        info->empty_rows = (int32_t)empty;
+        info->grid = (int32_t)gridDim.x;
+        info->reserved0 = 0;
+        info->reserved1 = 0.0;
+        info->reserved2 = 0.0;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512)
+k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int* counter, float tol,
+                  int64_t max_iter, int refresh) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ BatchShared sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = sh.unit;
+        __syncthreads();
+        if (u >= nunits) break;
+        // system of unit u: last s with unit_begin <= u (table ordered by unit_begin)
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (table[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const BatchSys S = table[lo];
+        solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh);
+    }
+}
+
+inline size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct BatchLayout {
+    size_t sort, gscr, table, counter, total;
+    std::vector<size_t> At, Bt, N2, G;
+    std::vector<int> order;          // systems by decreasing d*n
+    int64_t mmax, dmax, nmax;
+};
+
+int batch_layout(const csk_system* sys, int nsys, BatchLayout* L) {
+    L->mmax = L->dmax = L->nmax = 0;
+    for (int s = 0; s < nsys; ++s) {
+        const csk_system& y = sys[s];
+        if (!y.A || !y.B || !y.Xout || !y.info) return CSK_EINVAL;
+        if (y.m < 1 || y.n < 1 || y.d < 1 || y.lda < y.n || y.nrhs < 1 || y.ldb < y.nrhs)
+            return CSK_EINVAL;
+        if (y.m > INT_MAX || y.n > INT_MAX || y.d > INT_MAX) return CSK_ENOMEM;
+        L->mmax = std::max(L->mmax, y.m);
+        L->dmax = std::max(L->dmax, y.d);
+        L->nmax = std::max(L->nmax, y.n);
+    }
+    size_t o = 0;
+    L->sort = o;  o += a256(sort_scratch_bytes(L->mmax, L->dmax));
+    L->gscr = o;  o += a256(gram_scratch_bytes((int)L->dmax, (int)L->nmax));
+    L->table = o; o += a256((size_t)nsys * sizeof(BatchSys));
+    L->counter = o; o += 256;
+    L->At.resize(nsys); L->Bt.resize(nsys); L->N2.resize(nsys); L->G.resize(nsys);
+    for (int s = 0; s < nsys; ++s) {
+        const csk_system& y = sys[s];
+        L->At[s] = o; o += a256((size_t)y.d * y.n * 4);
+        L->Bt[s] = o; o += a256((size_t)y.d * y.nrhs * 4);
+        L->N2[s] = o; o += a256((size_t)y.d * 8);
+        L->G[s] = o;  o += a256((size_t)y.d * gram_ld((int)y.d) * 4);
+    }
+    L->total = o;
+    L->order.resize(nsys);
+    std::iota(L->order.begin(), L->order.end(), 0);
+    std::stable_sort(L->order.begin(), L->order.end(), [&](int a, int b) {
+        return sys[a].d * sys[a].n > sys[b].d * sys[b].n;
+    });
+    return CSK_OK;
+}
+
+}  // namespace
+
+size_t batched_workspace_bytes(const csk_system* sys, int nsys) {
+    BatchLayout L;
+    if (!sys || nsys < 1 || batch_layout(sys, nsys, &L) != CSK_OK) return 0;
+    return L.total;
+}
+
+int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int* threads,
+                 int* grid, size_t* smem) {
+    DevInfo di;
+    if (dev_info(&di) != 0) return CSK_ECUDA;
+    const size_t need = (size_t)(2 * ((dmax + 3) & ~3) + 2 * ((nmax + 3) & ~3)) * 4;
+    if (need + sizeof(BatchShared) + 1024 > (size_t)di.smem_optin) return CSK_EUNSUPPORTED;
+    int t = threads_req > 0 ? threads_req : (dmax >= 4096 ? 512 : 256);
+    if (t < 64 || t > 512 || (t & 31)) return CSK_EINVAL;
+    if (ensure_smem_attr((const void*)k_iterate_batched, need) != cudaSuccess) return CSK_ECUDA;
+    int per_sm = 0;
+    if (cached_occupancy((const void*)k_iterate_batched, t, need, &per_sm) != cudaSuccess ||
+        per_sm < 1)
+        return CSK_EUNSUPPORTED;
+    *threads = t;
+    *grid = grid_req > 0 ? grid_req : per_sm * di.sms;
+    *smem = need;
+    return CSK_OK;
+}
+
+int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* ws, size_t ws_bytes,
+                   cudaStream_t st) {
+    BatchLayout L;
+    int rc = batch_layout(sys, nsys, &L);
+    if (rc != CSK_OK) return rc;
+    if (ws_bytes < L.total) return CSK_EINVAL;
+    int threads = 0, grid = 0;
+    size_t smem = 0;
+    rc = plan_batched(L.dmax, L.nmax, p->threads, p->grid, &threads, &grid, &smem);
+    if (rc != CSK_OK) return rc;
+    char* w = static_cast<char*>(ws);
+    SortScratch s;
+    carve_sort_scratch(w + L.sort, L.mmax, L.dmax, &s);
+    std::vector<BatchSys> table(nsys);
+    int units = 0;
+    for (int q = 0; q < nsys; ++q) {
+        const int i = L.order[q];
+        const csk_system& y = sys[i];
+        float* At = reinterpret_cast<float*>(w + L.At[i]);
+        float* Bt = reinterpret_cast<float*>(w + L.Bt[i]);
+        double* N2 = reinterpret_cast<double*>(w + L.N2[i]);
+        float* G = reinterpret_cast<float*>(w + L.G[i]);
+        if (launch_bucket_sort(y.m, y.d, y.seed, s, st) != cudaSuccess) return CSK_ECUDA;
+        if (launch_segsum(CSK_F32, y.A, y.lda, (int)y.n, y.B, y.ldb, y.nrhs, s.perm, s.off,
+                          (int)y.d, y.seed, At, Bt, N2, st) != cudaSuccess)
+            return CSK_ECUDA;
+        if (launch_gram_split_bf16(At, (int)y.d, (int)y.n, N2, G, gram_ld((int)y.d), w + L.gscr,
+                                   nullptr, st) != cudaSuccess)
+            return CSK_ECUDA;
+        BatchSys& e = table[q];
+        e.At = At; e.Bt = Bt; e.N2 = N2; e.G = G;
+        e.X0 = static_cast<const float*>(y.X0);
+        e.Xstar = static_cast<const float*>(y.Xstar);
+        e.Xout = static_cast<float*>(y.Xout);
+        e.info = y.info;
+        e.ldg = gram_ld((int)y.d);
+        e.d = (int)y.d; e.n = (int)y.n; e.nrhs = y.nrhs; e.unit_begin = units;
+        units += y.nrhs;
+    }
+    BatchSys* dtable = reinterpret_cast<BatchSys*>(w + L.table);
+    for (int first = 0; first < nsys; first += kTableChunk) {
+        TableChunk c;
+        c.first = first;
+        c.count = std::min(kTableChunk, nsys - first);
+        for (int i = 0; i < c.count; ++i) c.e[i] = table[first + i];
+        k_write_table<<<1, kTableChunk, 0, st>>>(c, dtable);
+        note_launches(1);
+    }
+    int* counter = reinterpret_cast<int*>(w + L.counter);
+    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return CSK_ECUDA;
+    k_iterate_batched<<<grid, threads, smem, st>>>(dtable, nsys, units, counter, (float)p->tol,
+                                                   p->max_iter, p->refresh_every);
+    note_launches(1);
+    return cudaGetLastError() == cudaSuccess ? CSK_OK : CSK_ECUDA;
+}
+
+}  // namespace csk

@@ -346,7 +346,7 @@ cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* 
     CUtensorMap mh, ml;
     if (!make_map(&mh, hi, dp, kp) || !make_map(&ml, lo, dp, kp)) return cudaErrorInvalidValue;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_attr((const void*)k_gram_tc, smem);
     if (e != cudaSuccess) return e;
     const int nt = dp / BM;
     k_gram_tc<<<dim3(nt, nt), 128, smem, st>>>(mh, ml, d, kp / BK, G, ldg, info);

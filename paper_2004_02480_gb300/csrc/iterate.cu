@@ -585,10 +585,10 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
     else if (p.dtype == CSK_F64) fn = (void*)k_iterate_gemv<double>;
     else fn = (void*)k_iterate_gemv<float>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    cudaError_t e = ensure_smem_attr(fn, cfg.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cfg.threads, cfg.smem);
+    e = cached_occupancy(fn, cfg.threads, cfg.smem, &per_sm);
     if (e != cudaSuccess) return e;
     DevInfo di;
     dev_info(&di);

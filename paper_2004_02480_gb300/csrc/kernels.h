@@ -17,6 +17,13 @@ struct DevInfo {
 };
 int dev_info(DevInfo* out);
 
+// Kernel attributes and occupancy, set / queried once per (device, kernel,
+// value) and cached: cudaFuncSetAttribute may not be called while a stream is
+// being captured into a CUDA graph, so after a first (uncaptured) call the
+// launch sequences make no such call.
+cudaError_t ensure_smem_attr(const void* fn, size_t smem);
+cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_sm);
+
 // Count of kernels enqueued by the library (csk_kernel_launches).
 void note_launches(int k);
 
@@ -89,6 +96,11 @@ cudaError_t launch_final_check(int dtype, const void* At, int64_t ld, int d, int
                                const void* xstar, double* partials, csk_info* info,
                                cudaStream_t st);
 size_t final_check_partials(int d);
+
+// -------------------------------------------------------------- batched
+size_t batched_workspace_bytes(const csk_system* sys, int nsys);
+int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* ws, size_t ws_bytes,
+                   cudaStream_t st);
 
 // ----------------------------------------------------------------- Gram
 // G = At At^T (d x d, FP32) from split BF16 operands on the tensor cores;

@@ -8,7 +8,8 @@
 //   k_bucket_sort perm: each bucket sorted by row index, i.e. the rows in
 //                 (h(i), i) order -- unique, so independent of atomic order
 //   k_segsum      At_j = sum_{p in bucket j, ascending} D_ii A_i, Bt likewise,
-//                 and ||At_j||^2 in FP64: one warp per bucket, 128-bit loads.
+//                 and ||At_j||^2 in FP64: one CTA per bucket, a warp per
+//                 128-column chunk, 128-bit loads, 4 rows in flight per warp.
 #include <climits>
 #include <cstdio>
 
@@ -219,84 +220,97 @@ __device__ __forceinline__ void vstore(T* p, const T (&in)[V]) {
     *reinterpret_cast<VT*>(p) = v;
 }
 
-// Signed sum of the rows perm[p0..p1) of src (ncols columns) into dst, one
-// warp, ascending p per column.  Returns this lane's sum of squares (FP64).
+// Signed sum of the rows perm[p0..p1) of src, columns [c0, c0 + 32 V CPL)
+// of ncols, into dst, by one warp, ascending p in every column.  Returns this
+// lane's sum of squares of its finished columns (FP64).
 template <typename T, int V, int CPL, int U>
-__device__ __forceinline__ double seg_rows(const T* __restrict__ src, int64_t ld, int ncols,
-                                           const int32_t* __restrict__ perm, int32_t p0,
-                                           int32_t p1, uint64_t seed, T* __restrict__ dst) {
+__device__ __forceinline__ double seg_chunk(const T* __restrict__ src, int64_t ld, int ncols, int c0,
+                                            const int32_t* __restrict__ perm, int32_t p0,
+                                            int32_t p1, uint64_t seed, T* __restrict__ dst) {
     const int lane = lane_id();
-    double sq = 0.0;
-    for (int c0 = 0; c0 < ncols; c0 += 32 * V * CPL) {
-        T acc[CPL][V];
+    T acc[CPL][V];
 #pragma unroll
-        for (int c = 0; c < CPL; ++c)
+    for (int c = 0; c < CPL; ++c)
 #pragma unroll
-            for (int q = 0; q < V; ++q) acc[c][q] = T(0);
-        for (int32_t pb = p0; pb < p1; pb += 32) {
-            const int32_t myrow = (pb + lane < p1) ? perm[pb + lane] : 0;
-            const int myneg = row_negative(row_hash(seed, (uint64_t)myrow)) ? 1 : 0;
-            const int cnt = min(32, p1 - pb);
-            for (int q0 = 0; q0 < cnt; q0 += U) {
-                T vals[U][CPL][V];
-                int neg[U];
+        for (int q = 0; q < V; ++q) acc[c][q] = T(0);
+    for (int32_t pb = p0; pb < p1; pb += 32) {
+        const int32_t myrow = (pb + lane < p1) ? perm[pb + lane] : 0;
+        const int myneg = row_negative(row_hash(seed, (uint64_t)myrow)) ? 1 : 0;
+        const int cnt = min(32, p1 - pb);
+        for (int q0 = 0; q0 < cnt; q0 += U) {
+            T vals[U][CPL][V];
+            int neg[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int32_t row = __shfl_sync(0xffffffffu, myrow, (q0 + u) & 31);
-                    neg[u] = __shfl_sync(0xffffffffu, myneg, (q0 + u) & 31);
-                    const bool valid = q0 + u < cnt;
-                    const T* rp = src + (int64_t)row * ld;
+            for (int u = 0; u < U; ++u) {
+                const int32_t row = __shfl_sync(0xffffffffu, myrow, (q0 + u) & 31);
+                neg[u] = __shfl_sync(0xffffffffu, myneg, (q0 + u) & 31);
+                const bool valid = q0 + u < cnt;
+                const T* rp = src + (int64_t)row * ld;
 #pragma unroll
-                    for (int c = 0; c < CPL; ++c) {
-                        const int col = c0 + (c * 32 + lane) * V;
-                        if (valid && col < ncols) {
-                            vload<T, V>(rp + col, vals[u][c]);
-                        } else {
+                for (int c = 0; c < CPL; ++c) {
+                    const int col = c0 + (c * 32 + lane) * V;
+                    if (valid && col < ncols) {
+                        vload<T, V>(rp + col, vals[u][c]);
+                    } else {
 #pragma unroll
-                            for (int q = 0; q < V; ++q) vals[u][c][q] = T(0);
-                        }
+                        for (int q = 0; q < V; ++q) vals[u][c][q] = T(0);
                     }
                 }
+            }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (q0 + u < cnt) {
+            for (int u = 0; u < U; ++u) {
+                if (q0 + u < cnt) {
 #pragma unroll
-                        for (int c = 0; c < CPL; ++c)
+                    for (int c = 0; c < CPL; ++c)
 #pragma unroll
-                            for (int q = 0; q < V; ++q)
-                                acc[c][q] = neg[u] ? acc[c][q] - vals[u][c][q]
-                                                   : acc[c][q] + vals[u][c][q];
-                    }
+                        for (int q = 0; q < V; ++q)
+                            acc[c][q] = neg[u] ? acc[c][q] - vals[u][c][q] : acc[c][q] + vals[u][c][q];
                 }
             }
         }
+    }
+    double sq = 0.0;
 #pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int col = c0 + (c * 32 + lane) * V;
-            if (col < ncols) {
-                vstore<T, V>(dst + col, acc[c]);
+    for (int c = 0; c < CPL; ++c) {
+        const int col = c0 + (c * 32 + lane) * V;
+        if (col < ncols) {
+            vstore<T, V>(dst + col, acc[c]);
 #pragma unroll
-                for (int q = 0; q < V; ++q) sq += (double)acc[c][q] * (double)acc[c][q];
-            }
+            for (int q = 0; q < V; ++q) sq += (double)acc[c][q] * (double)acc[c][q];
         }
     }
     return sq;
 }
 
+// One CTA per bucket (grid-stride): warp w sums the column chunks w, w + W,
+// ... of the bucket's rows; warp 0 also sums the right-hand sides.  The FP64
+// row norm is combined across warps in a fixed order.
 template <typename T, int V, int CPL, int U>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_segsum(const T* __restrict__ A, int64_t lda, int n, const T* __restrict__ B, int64_t ldb,
          int nrhs, const int32_t* __restrict__ perm, const int32_t* __restrict__ off, int d,
          uint64_t seed, T* __restrict__ At, T* __restrict__ Bt, double* __restrict__ N2) {
-    const int warps_per_block = blockDim.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
-    for (int64_t j = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5); j < d; j += nwarps) {
+    __shared__ double part[4];
+    constexpr int CW = 32 * V * CPL;                 // columns per chunk
+    const int W = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    for (int64_t j = blockIdx.x; j < d; j += gridDim.x) {
         const int32_t p0 = off[j], p1 = off[j + 1];
-        double sq = seg_rows<T, V, CPL, U>(A, lda, n, perm, p0, p1, seed, At + j * (int64_t)n);
+        double sq = 0.0;
+        for (int c0 = warp * CW; c0 < n; c0 += W * CW)
+            sq += seg_chunk<T, V, CPL, U>(A, lda, n, c0, perm, p0, p1, seed, At + j * (int64_t)n);
+        if (warp == 0 && B && nrhs > 0)
+            for (int c0 = 0; c0 < nrhs; c0 += 64)
+                (void)seg_chunk<T, 1, 2, 4>(B, ldb, nrhs, c0, perm, p0, p1, seed,
+                                            Bt + j * (int64_t)nrhs);
         sq = warp_sum(sq);
-        if (N2 && lane_id() == 0) N2[j] = sq;
-        if (B && nrhs > 0)
-            (void)seg_rows<T, 1, 2, 2>(B, ldb, nrhs, perm, p0, p1, seed, Bt + j * (int64_t)nrhs);
+        if (lane_id() == 0) part[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0 && N2) {
+            double t = 0.0;
+            for (int w = 0; w < W; ++w) t += part[w];
+            N2[j] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -383,28 +397,29 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int n, const vo
                           cudaStream_t st) {
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
-    const int threads = 256;
-    int64_t blocks = ((int64_t)d + 7) / 8;
-    if (blocks > (int64_t)di.sms * 32) blocks = (int64_t)di.sms * 32;
+    int64_t blocks = d;
+    if (blocks > (int64_t)di.sms * 64) blocks = (int64_t)di.sms * 64;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
+    // warps per bucket: one per column chunk, at most 4
+    auto warps_for = [&](int cw) { int w = (n + cw - 1) / cw; return w < 1 ? 1 : (w > 4 ? 4 : w); };
     if (dtype == CSK_F32) {
         const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
         if (vec)
-            k_segsum<float, 4, 4, 2><<<(int)blocks, threads, 0, st>>>(
+            k_segsum<float, 4, 1, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
                 (const float*)A, lda, n, (const float*)B, ldb, nrhs, perm, off, d, seed,
                 (float*)At, (float*)Bt, N2);
         else
-            k_segsum<float, 1, 8, 2><<<(int)blocks, threads, 0, st>>>(
+            k_segsum<float, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
                 (const float*)A, lda, n, (const float*)B, ldb, nrhs, perm, off, d, seed,
                 (float*)At, (float*)Bt, N2);
     } else {
         const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
         if (vec)
-            k_segsum<double, 2, 4, 2><<<(int)blocks, threads, 0, st>>>(
+            k_segsum<double, 2, 2, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
                 (const double*)A, lda, n, (const double*)B, ldb, nrhs, perm, off, d, seed,
                 (double*)At, (double*)Bt, N2);
         else
-            k_segsum<double, 1, 8, 2><<<(int)blocks, threads, 0, st>>>(
+            k_segsum<double, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
                 (const double*)A, lda, n, (const double*)B, ldb, nrhs, perm, off, d, seed,
                 (double*)At, (double*)Bt, N2);
     }

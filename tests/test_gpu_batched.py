@@ -1,0 +1,117 @@
+"""GPU parity of csk_solve_batched (many systems x many right-hand sides in one
+persistent launch).
+
+Each (system, right-hand side) pair must reach RES <= 1e-6 with IT close to
+the FP64 oracle's on the same (bit-exact) sketch, agree with the single-system
+GPU solve at the same accuracy, and -- with the CTA shape fixed -- give the
+same bits alone and inside a larger batch (per-pair arithmetic does not depend
+on the co-scheduled work).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2004_02480_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def csk():
+    from paper_2004_02480_gb300 import build, csk as _csk
+    build.build()
+    return _csk
+
+
+def _batch(csk, shapes, seed0=0):
+    batch, host = [], []
+    for i, (m, n, d, R) in enumerate(shapes):
+        s = synth.gaussian_multi_rhs(m, n, R, seed0 + i, np.float32)
+        batch.append(csk.BatchSystem(A=torch.from_numpy(s.A).to(DEV), B=torch.from_numpy(s.b).to(DEV),
+                                     d=d, seed=seed0 + 100 + i,
+                                     Xstar=torch.from_numpy(s.x_star.astype(np.float32)).to(DEV)))
+        host.append(s)
+    return batch, host
+
+
+SHAPES = [(20000, 120, 1200, 3), (5000, 50, 500, 8), (12000, 200, 2000, 2), (3000, 20, 160, 5),
+          (2000, 33, 330, 1), (8000, 77, 770, 4)]
+
+
+def test_batched_matches_oracle(csk):
+    batch, host = _batch(csk, SHAPES)
+    p = csk.csk_params_default(max_iter=20000)
+    out = csk.csk_solve_batched(batch, p)
+    for (m, n, d, R), y, s, (X, infos) in zip(SHAPES, batch, host, out):
+        h, sg = oracle.count_sketch_map(y.seed, m, d)
+        At, Bt = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+        Xh = X.cpu().numpy()
+        for r in range(R):
+            inf = infos[r]
+            ref = oracle.mwrk(At.astype(np.float64), Bt[:, r].astype(np.float64),
+                              x_star=s.x_star[:, r], nthreads=4)
+            assert inf["status"] == 0 and ref.status == 0, (m, n, d, r, inf)
+            assert inf["rse"] <= 1e-6
+            xs32 = s.x_star[:, r].astype(np.float32).astype(np.float64)
+            rse = np.sum((Xh[:, r] - xs32) ** 2) / np.sum(xs32 ** 2)
+            assert abs(inf["rse"] - rse) <= 1e-9 * rse
+            assert abs(inf["iters"] - ref.iters) <= max(3, 0.1 * ref.iters), (inf["iters"], ref.iters)
+            rr, res = oracle.final_check(At.astype(np.float64), Bt[:, r].astype(np.float64), Xh[:, r])
+            assert abs(inf["resid"] - res) <= 1e-6 * res + 1e-9
+
+
+def test_batched_agrees_with_single_solve(csk):
+    shapes = SHAPES[:3]
+    batch, host = _batch(csk, shapes, seed0=10)
+    out = csk.csk_solve_batched(batch, csk.csk_params_default())
+    for (m, n, d, R), y, s, (X, infos) in zip(shapes, batch, host, out):
+        for r in range(R):
+            p = csk.csk_params_default(d=d, seed=y.seed, path=csk.GRAM)
+            b = torch.from_numpy(np.ascontiguousarray(s.b[:, r])).to(DEV)
+            xs = torch.from_numpy(s.x_star[:, r].astype(np.float32)).to(DEV)
+            x1, inf1 = csk.csk_solve(y.A, b, p, x_star=xs)
+            assert inf1["status"] == 0 and infos[r]["status"] == 0
+            diff = np.sum((x1.cpu().numpy() - X[:, r].cpu().numpy()) ** 2) / np.sum(s.x_star[:, r] ** 2)
+            assert diff <= 4e-6
+
+
+def test_alone_equals_in_the_mix(csk):
+    """With the CTA shape fixed, a pair's result does not depend on which
+    other pairs share the launch or on which CTA ran it."""
+    batch, host = _batch(csk, SHAPES, seed0=20)
+    p = csk.csk_params_default(threads=256)
+    mix = [(X.cpu().clone(), [i["iters"] for i in infos]) for X, infos in csk.csk_solve_batched(batch, p)]
+    for k in (0, 3, 5):
+        y = batch[k]
+        alone = csk.BatchSystem(A=y.A, B=y.B, d=y.d, seed=y.seed, Xstar=y.Xstar)
+        (X1, inf1), = csk.csk_solve_batched([alone], p)
+        assert torch.equal(X1.cpu(), mix[k][0])
+        assert [i["iters"] for i in inf1] == mix[k][1]
+
+
+def test_batched_graph_capture_replay(csk):
+    """The batched call makes no synchronising call, so it can be captured
+    in a CUDA graph and replayed with the same results."""
+    batch, host = _batch(csk, SHAPES[:4], seed0=30)
+    p = csk.csk_params_default(threads=256)
+    ws = torch.empty(csk.csk_solve_batched_workspace_size(batch), dtype=torch.uint8, device=DEV)
+    ref = [(X.cpu().clone()) for X, _ in csk.csk_solve_batched(batch, p, ws=ws)]
+    for y in batch:
+        y.Xout.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        csk.csk_solve_batched(batch, p, ws=ws, sync=False)   # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        csk.csk_solve_batched(batch, p, ws=ws, sync=False)
+    for y in batch:
+        y.Xout.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for y, X in zip(batch, ref):
+        assert torch.equal(y.Xout.cpu(), X)
