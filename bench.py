@@ -221,12 +221,15 @@ def main():
     b = torch.from_numpy(s.b).to(dev)
     xs = torch.from_numpy(s.x_star.astype(np.float32)).to(dev)
     params = csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV)
+    from paper_2004_02480_gb300 import autotune
+    tuned = autotune.tune_solve(A, b, params, x_star=xs)     # grid and loop variant, untimed
     ws = csk._workspace(csk.csk_solve_workspace_size(M, N_COLS, csk.CSK_F32, params), dev)
     x = torch.empty(N_COLS, dtype=torch.float32, device=dev)
     K, W = args.steps, args.warmup
     infos = torch.empty((K, 64), dtype=torch.uint8, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
-    pk = [csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV) for _ in range(K)]
+    pk = [csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV, grid=params.grid,
+                                 gemv_variant=params.gemv_variant) for _ in range(K)]
     for i in range(K):
         csk.set_stage_events(pk[i], ev[i])
 
@@ -316,6 +319,9 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1), paper Section 3 recipe)",
         "config": {"workload": WORKLOAD, "m": M, "n": N_COLS, "d": D, "tol": TOL, "path": "gemv",
                    "parallelism": f"replicas x{world} (independent systems)",
+                   "loop": {"grid": tuned["grid"], "variant": ["auto", "shared-memory rows",
+                                                               "register rows"][tuned["gemv_variant"]],
+                            "autotuned_us_per_step": tuned["us_per_step"]},
                    "l2": "inputs larger than L2 (A = 200 MB > 129 MB)"},
         "valid": bool(ok),
         "breakdown": {"sketch_ms": sk_ms, "iterate_ms": it_ms, "check_ms": float(np.mean(st_check)),

@@ -44,7 +44,7 @@ class csk_params(ctypes.Structure):
                 ("ik_log", ctypes.c_void_p), ("ik_log_len", ctypes.c_int64),
                 ("grid", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("x_log", ctypes.c_void_p), ("x_log_len", ctypes.c_int64),
-                ("threads", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("gemv_variant", ctypes.c_int32),
                 ("stage_events", ctypes.c_void_p * 5)]
 
 

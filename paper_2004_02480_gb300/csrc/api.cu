@@ -75,10 +75,12 @@ int check_stream_device(cudaStream_t st) {
     return sd == cur ? CSK_OK : CSK_EINVAL;
 }
 
-int resolve_path(int path, int dtype, int64_t d) {
-    if (path == CSK_RESID_AUTO) return CSK_RESID_GEMV;
-    (void)dtype; (void)d;
-    return path;
+// AUTO: GEMV while the sketch fits on chip across the SMs (shared memory or
+// registers, ~24 MB), else GRAM (FP32 only; an unsketched A stays GEMV).
+int resolve_path(int path, int dtype, int64_t d, int64_t n) {
+    if (path != CSK_RESID_AUTO) return path;
+    if (dtype != CSK_F32 || d == 0) return CSK_RESID_GEMV;
+    return d * n * 4 <= (int64_t)24 << 20 ? CSK_RESID_GEMV : CSK_RESID_GRAM;
 }
 
 int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk_params* params,
@@ -91,9 +93,10 @@ int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk
     if (params->x_log_len < 0 || (params->x_log_len > 0 && !params->x_log)) return CSK_EINVAL;
     if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_AUTO) return CSK_EINVAL;
     if (params->grid < 0 || params->refresh_every < 0) return CSK_EINVAL;
+    if (params->gemv_variant < 0 || params->gemv_variant > 2) return CSK_EINVAL;
     if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
-    const int path = resolve_path(params->path, dtype, d);
+    const int path = resolve_path(params->path, dtype, d, n);
     if (path == CSK_RESID_GRAM && dtype != CSK_F32) return CSK_EUNSUPPORTED;
     if (path == CSK_RESID_GRAM && d == 0) return CSK_EUNSUPPORTED;   // an m x m Gram is pointless
     return CSK_OK;
@@ -123,10 +126,14 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
                   const csk_params* params, const void* x0, const void* x_star, void* x_out,
                   csk_info* info, void* ws, const SolveLayout& L, cudaStream_t st) {
     const int64_t d = params->d;
-    const int path = resolve_path(params->path, dtype, d);
+    const int path = resolve_path(params->path, dtype, d, n);
     const int rows = (int)(d > 0 ? d : m);
     IterConfig cfg;
-    int rc = plan_iterate(path, dtype, rows, (int)n, params->grid, &cfg);
+    const int64_t ld_it = d > 0 ? n : lda;
+    const bool vec_ok = (ld_it % 4 == 0) &&
+                        (d > 0 || reinterpret_cast<uintptr_t>(A) % 16 == 0);
+    int rc = plan_iterate(path, dtype, rows, (int)n, params->grid, params->gemv_variant, vec_ok,
+                          &cfg);
     if (rc != CSK_OK) return rc;
     if (cfg.grid > kMaxIterGrid) return CSK_EUNSUPPORTED;
 
@@ -345,7 +352,7 @@ size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_p
     if (!params || m < 1 || n < 1 || params->d < 0) return 0;
     if (dtype != CSK_F32 && dtype != CSK_F64) return 0;
     SolveLayout L;
-    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d, n), &L);
     return L.total;
 }
 
@@ -356,7 +363,7 @@ int csk_solve(const void* A, int64_t m, int64_t n, int64_t lda, const void* b, i
     int rc = check_solve_args(m, n, lda, dtype, params, ws);
     if (rc != CSK_OK) return rc;
     SolveLayout L;
-    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d, n), &L);
     if (ws_bytes < L.total) return CSK_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = check_stream_device(st);
@@ -382,7 +389,7 @@ int csk_solve_host(const void* A_host, int64_t m, int64_t n, int64_t lda, const 
     HostStaging H;
     host_staging(m, n, dtype, &H);
     SolveLayout L;
-    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d), &L);
+    solve_layout(m, n, dtype, params->d, resolve_path(params->path, dtype, params->d, n), &L);
     if (ws_bytes < H.total + L.total) return CSK_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = check_stream_device(st);

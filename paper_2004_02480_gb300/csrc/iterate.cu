@@ -70,6 +70,24 @@ __device__ __forceinline__ void warp_reduce(Red<T>& c) {
     }
 }
 
+// Warp argmax of FP32 candidates with the integer reduction unit: the key is
+// mapped to a monotone 32-bit code (NaN highest, "no candidate" lowest), the
+// maximal code and then the smallest row among its holders are found with
+// redux.sync, and the winner's step length is fetched from its lane.  Same
+// ordering as better(); the statistic is summed with a shuffle tree.
+__device__ __forceinline__ void warp_reduce(Red<float>& c) {
+    const uint32_t code = c.key != c.key ? 0xFFFFFFFFu
+                                         : (c.key < 0.0f ? 0u : __float_as_uint(c.key) + 1u);
+    const uint32_t best = __reduce_max_sync(0xffffffffu, code);
+    const uint32_t row = __reduce_min_sync(0xffffffffu, code == best ? (uint32_t)c.idx : 0xFFFFFFFFu);
+    const unsigned win = __ballot_sync(0xffffffffu, code == best && (uint32_t)c.idx == row);
+    const int wl = __ffs(win) - 1;
+    c.key = __shfl_sync(0xffffffffu, c.key, wl);
+    c.alpha = __shfl_sync(0xffffffffu, c.alpha, wl);
+    c.idx = (int32_t)row;
+    c.stat = warp_sum(c.stat);
+}
+
 // CTA-wide reduction with a single barrier: warps post their partial results
 // in one of two shared buffers (alternating between calls), then every warp
 // reduces the posted partials itself, so all threads end with the same bits.
@@ -355,6 +373,176 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     finish(p.info, status, k);
 }
 
+// ------------------------------------------------ GEMV path, registers
+// FP32 variant for n <= 128 * CPL (n % 4 == 0) and at most kWarps * RPW rows
+// per CTA: warp w keeps rows w, w + kWarps, ... of At in registers (lane l
+// holds the float4 columns l, l + 32, ...), and every warp keeps x for the
+// same columns in registers, so a step touches no shared memory except the
+// CTA reduction.  The projection is applied by every warp to its own copy
+// of x (identical arithmetic everywhere); float4 column c4 of the
+// ||x - x*||^2 statistic is counted by CTA c4 % grid alone.
+template <int RPW>
+__device__ __forceinline__ void warp_sum_rows(float (&v)[RPW]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+}
+
+template <int RPW, int CPL>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_iterate_gemv_reg(IterProblem p, int R) {
+    __shared__ RedShared<float> sh;
+    int par = 0;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int n = p.n, d = p.d, n4 = n >> 2;
+    const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
+    const float* At = static_cast<const float*>(p.At);
+    const float* bt = static_cast<const float*>(p.bt);
+    const float* x0 = static_cast<const float*>(p.x0);
+    const float* xstar = static_cast<const float*>(p.xstar);
+    const bool stat_owner = (b == 0 && warp == 0);
+
+    float4 a[RPW][CPL];
+    float btu[RPW], wu[RPW];
+    bool has[RPW];
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+        const int q = warp + kWarps * u;
+        has[u] = q < nr;
+        btu[u] = has[u] ? bt[r0 + q] : 0.0f;
+        wu[u] = has[u] ? weight_of<float>(p.N2[r0 + q]) : -1.0f;
+        const float4* row = reinterpret_cast<const float4*>(At + (int64_t)(r0 + (has[u] ? q : 0)) * p.ld);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int c4 = lane + 32 * i;
+            a[u][i] = (has[u] && c4 < n4) ? row[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    float4 xr[CPL], xsr[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        const int c4 = lane + 32 * i;
+        xr[i] = (x0 && c4 < n4) ? reinterpret_cast<const float4*>(x0)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xsr[i] = (xstar && c4 < n4) ? reinterpret_cast<const float4*>(xstar)[c4]
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float threshold = (float)(p.tol * *p.stop_norm);
+    const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    uint32_t round = 0;
+    int64_t k = 0;
+    int status = CSK_OK;
+    for (;;) {
+        float dot[RPW];
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                acc = fmaf(a[u][i].x, xr[i].x, acc);
+                acc = fmaf(a[u][i].y, xr[i].y, acc);
+                acc = fmaf(a[u][i].z, xr[i].z, acc);
+                acc = fmaf(a[u][i].w, xr[i].w, acc);
+            }
+            dot[u] = acc;
+        }
+        warp_sum_rows<RPW>(dot);
+        Red<float> c;
+        c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+            if (has[u]) {
+                const float r = btu[u] - dot[u];
+                if (!(wu[u] < 0.0f)) {
+                    const float key = r * r * wu[u];
+                    const int j = r0 + warp + kWarps * u;
+                    if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r * wu[u]; c.idx = j; }
+                }
+                if (!xstar && lane == 0) c.stat += r * r;
+            }
+        }
+        if (xstar && warp == 0) {
+            // float4 column c4 is counted by CTA c4 % G only
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
+                    const float ex = xr[i].x - xsr[i].x, ey = xr[i].y - xsr[i].y;
+                    const float ez = xr[i].z - xsr[i].z, ew = xr[i].w - xsr[i].w;
+                    c.stat += ex * ex + ey * ey + ez * ez + ew * ew;
+                }
+            }
+        }
+        c = block_reduce_wu(c, sh, par);
+        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
+            status = CSK_ETIMEOUT;
+            break;
+        }
+        ++round;
+        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
+        if (dec != INT_MIN) { status = dec; break; }
+        if (stat_owner && lane == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
+        if (stat_owner && p.x_log && k < p.x_log_len)
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+                if (lane + 32 * i < n4)
+                    reinterpret_cast<float4*>(static_cast<float*>(p.x_log) + k * n)[lane + 32 * i] = xr[i];
+        // projection onto row i_k, applied by every warp to its copy of x
+        const float4* arow = reinterpret_cast<const float4*>(At + (int64_t)c.idx * p.ld);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int c4 = lane + 32 * i;
+            if (c4 < n4) {
+                const float4 v = __ldg(arow + c4);
+                xr[i].x = fmaf(c.alpha, v.x, xr[i].x);
+                xr[i].y = fmaf(c.alpha, v.y, xr[i].y);
+                xr[i].z = fmaf(c.alpha, v.z, xr[i].z);
+                xr[i].w = fmaf(c.alpha, v.w, xr[i].w);
+            }
+        }
+        ++k;
+    }
+    if (stat_owner) {
+        float4* xo = reinterpret_cast<float4*>(p.x_out);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+            if (lane + 32 * i < n4) xo[lane + 32 * i] = xr[i];
+    }
+    finish(p.info, status, k);
+}
+
+// Register-resident variants: (rows per warp, float4 per lane per row).
+#define CSK_REG_VARIANTS(X) \
+    X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(6, 1) X(8, 1) \
+    X(1, 2) X(2, 2) X(3, 2) X(4, 2) X(6, 2) X(8, 2) \
+    X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4)
+
+const void* reg_kernel(int rpw, int cpl) {
+#define CSK_PICK(RPWv, CPLv) \
+    if (rpw == RPWv && cpl == CPLv) return (const void*)k_iterate_gemv_reg<RPWv, CPLv>;
+    CSK_REG_VARIANTS(CSK_PICK)
+#undef CSK_PICK
+    return nullptr;
+}
+
+// Smallest instantiated (rows per warp, float4 per lane) covering the shape.
+bool reg_shape(int rows_per_cta, int n, int* rpw, int* cpl) {
+    if (n % 4 != 0) return false;
+    const int need_c = (n / 4 + 31) / 32;
+    const int need_r = (rows_per_cta + kWarps - 1) / kWarps;
+    const int cs[] = {1, 2, 4};
+    const int rs[] = {1, 2, 3, 4, 5, 6, 8};
+    for (int c : cs) {
+        if (c < need_c) continue;
+        for (int r : rs) {
+            if (r < need_r) continue;
+            if (reg_kernel(r, c)) { *rpw = r; *cpl = c; return true; }
+        }
+        return false;
+    }
+    return false;
+}
+
 // ------------------------------------------------------------ GRAM path
 // Shared memory: r (Rpad) | w2 (Rpad) | x slice (spad) | x* slice (spad) |
 // full x for the refresh (npad)
@@ -546,7 +734,8 @@ int final_blocks(int d) {
 }  // namespace
 
 // ------------------------------------------------------------ host side
-int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cfg) {
+int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, bool vec_ok,
+                 IterConfig* cfg) {
     DevInfo di;
     if (dev_info(&di) != 0) return CSK_ECUDA;
     const int s = dtype == CSK_F64 ? 8 : 4;
@@ -576,15 +765,29 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cf
         cfg->cache_rows = (base + rows <= budget) ? 1 : 0;
         cfg->smem = base + (cfg->cache_rows ? rows : 0);
     }
+    cfg->reg_rpw = cfg->reg_cpl = 0;
+    if (path == CSK_RESID_GEMV && dtype == CSK_F32 && vec_ok && variant != 1) {
+        int rpw = 0, cpl = 0;
+        if (reg_shape(R, n, &rpw, &cpl)) {
+            cfg->reg_rpw = rpw;
+            cfg->reg_cpl = cpl;
+            cfg->cache_rows = 0;
+            cfg->smem = 0;
+        }
+    }
+    if (variant == 2 && cfg->reg_rpw == 0) return CSK_EUNSUPPORTED;
     if (cfg->smem > budget) return CSK_EUNSUPPORTED;
     return CSK_OK;
 }
 
 cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st) {
     void* fn;
+    const bool reg = cfg.reg_rpw > 0;
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
+    else if (reg) fn = const_cast<void*>(reg_kernel(cfg.reg_rpw, cfg.reg_cpl));
     else if (p.dtype == CSK_F64) fn = (void*)k_iterate_gemv<double>;
     else fn = (void*)k_iterate_gemv<float>;
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem_attr(fn, cfg.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -598,7 +801,8 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     void* args_gemv[] = {&pc, &R, &cache};
     void* args_gram[] = {&pc, &R};
     e = cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(cfg.threads),
-                                    path == CSK_RESID_GRAM ? args_gram : args_gemv, cfg.smem, st);
+                                    (path == CSK_RESID_GRAM || reg) ? args_gram : args_gemv,
+                                    cfg.smem, st);
     if (e == cudaSuccess) note_launches(1);
     return e;
 }

@@ -68,6 +68,8 @@ struct IterConfig {
     int threads = 256;
     int rows_per_cta = 0;
     int cache_rows = 0;     // At slice resident in shared memory (GEMV path)
+    int reg_rpw = 0;        // >0: register-resident GEMV variant, rows per warp
+    int reg_cpl = 0;        //     and float4 columns per lane
     size_t smem = 0;        // dynamic shared memory bytes
 };
 
@@ -87,7 +89,10 @@ struct IterProblem {
     csk_info* info;
 };
 
-int plan_iterate(int path, int dtype, int d, int n, int grid_req, IterConfig* cfg);
+// variant: 0 = library choice, 1 = shared-memory rows, 2 = register rows.
+// vec_ok: rows of At are 16-byte aligned with a leading dimension % 4 == 0.
+int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, bool vec_ok,
+                 IterConfig* cfg);
 cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st);
 
 // FP64 final check: info->rse, info->resid, info->empty_rows.

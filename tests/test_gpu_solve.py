@@ -210,3 +210,36 @@ def test_no_xstar_residual_stop(csk):
     ref = oracle.mwrk(At, bt, tol=1e-12)
     assert info["status"] == 0 and info["resid"] ** 2 <= 1.0001e-12
     assert abs(info["iters"] - ref.iters) <= 1
+
+
+def test_gemv_variants_agree(csk):
+    """Rows of At in shared memory (variant 1) and in registers (variant 2)
+    both follow the oracle's i_k prefix and converge with the same IT +-2 %."""
+    m, n, d, seed = 100000, 500, 5000, 3
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At32.astype(np.float64), bt32.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    its = []
+    for variant in (1, 2):
+        x, info, ik, X = _solve(csk, s, d, seed, log=20000, xlog=20000, gemv_variant=variant)
+        assert info["status"] == 0 and info["rse"] <= 1e-6
+        _compare_prefix(ik, ref, 1e-3)
+        _check_steps(At32, bt32, X, ik, min(info["iters"] - 1, 300), 2.0 ** -24)
+        its.append(info["iters"])
+    assert abs(its[0] - its[1]) <= 0.02 * ref.iters
+
+
+@pytest.mark.parametrize("grid", [50, 64, 100])
+def test_register_variant_small_and_timeout(csk, grid):
+    """Register-resident loop on a small sketch (one row per warp), and its
+    bounded wait: CTA 0 never publishes -> CSK_ETIMEOUT, context survives."""
+    s = synth.gaussian_system(3000, 40, 9, np.float32)
+    x, info, _ = _solve(csk, s, 400, 9, grid=grid, gemv_variant=2)
+    ref = oracle.csk(s.A.astype(np.float64), s.b.astype(np.float64), 400, 9, x_star=s.x_star)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+    assert abs(info["iters"] - ref.iters) <= max(3, 0.05 * ref.iters)
+    x, info, _ = _solve(csk, s, 400, 9, grid=grid, gemv_variant=2, spin_limit=20000,
+                        fault_inject=1)
+    assert info["status"] == -3
