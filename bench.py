@@ -200,6 +200,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=0, help="loop CTA count (0 = autotune)")
+    ap.add_argument("--variant", type=int, default=0, help="loop variant 1/2 (0 = autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -222,7 +224,11 @@ def main():
     xs = torch.from_numpy(s.x_star.astype(np.float32)).to(dev)
     params = csk.csk_params_default(d=D, seed=rank, tol=TOL, path=csk.GEMV)
     from paper_2004_02480_gb300 import autotune
-    tuned = autotune.tune_solve(A, b, params, x_star=xs)     # grid and loop variant, untimed
+    if args.grid > 0 and args.variant > 0:
+        params.grid, params.gemv_variant = args.grid, args.variant
+        tuned = {"grid": args.grid, "gemv_variant": args.variant, "us_per_step": None}
+    else:
+        tuned = autotune.tune_solve(A, b, params, x_star=xs)  # grid and loop variant, untimed
     ws = csk._workspace(csk.csk_solve_workspace_size(M, N_COLS, csk.CSK_F32, params), dev)
     x = torch.empty(N_COLS, dtype=torch.float32, device=dev)
     K, W = args.steps, args.warmup
@@ -302,7 +308,8 @@ def main():
     sk_ms = float(np.mean(st_sketch))
     sk_gbs = sketch_bytes(M, N_COLS, D) / (sk_ms * 1e-3) / 1e9
     src = _source_hash("paper_2004_02480_gb300/csrc/iterate.cu", "paper_2004_02480_gb300/csrc/common.cuh")
-    traffic = _traffic("k_iterate_gemv_100000x500_d5000", src)
+    traffic = _traffic(("k_iterate_gemv_reg" if tuned["gemv_variant"] == 2 else "k_iterate_gemv")
+                       + "_100000x500_d5000", src)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -328,11 +335,13 @@ def main():
                       "iters_mean": mean_it, "rse_max": max(r["rse"] for r in recs),
                       "grid": recs[0]["grid"],
                       "sketch_gbs": sk_gbs, "sketch_frac_of_" + peak_kind + "_hbm": sk_gbs / hbm},
-        "roofline": {"kernel": "k_iterate_gemv<float>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": ("k_iterate_gemv_reg" if tuned["gemv_variant"] == 2 else "k_iterate_gemv<float>"),
+                     "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
                      "traffic": traffic,
                      "note": "algorithmic bytes = (IT+1) residual evaluations x (4dn + 4(d+2n)); "
-                             "At stays in shared memory, so this is not DRAM traffic"},
+                             "At stays on chip (registers or shared memory), so this is not DRAM "
+                             "traffic; the loop is bound by the per-step exchange latency"},
         "e2e": {"value": world * E / te, "unit": UNIT,
                 "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes + 4 * N_COLS),
                 "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok)},

@@ -13,14 +13,15 @@
 // (k_gram_diag), which makes the residual update of the chosen row consistent
 // with the FP64 step length.
 //
-// k_gram_tc: one 128 x 128 output tile per CTA, 128 threads, 2 CTAs per SM.
-//   warp 0 / lane 0   TMA producer: 64-wide K chunks of the A-rows and B-rows
-//                     panels into a 3-stage ring (128B swizzle)
+// k_gram_tc: persistent, one CTA per SM, 128 x 256 output tiles.
+//   warp 0 / lane 0   TMA producer: 64-wide K chunks of the 128 A-rows and 256
+//                     B-rows into a 4-stage ring (128B swizzle)
 //   warp 1 / lane 0   MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
-//                     M = 128, N = 128, K = 16, accumulator in TMEM
-//   warp 2            TMEM allocator (128 columns)
-//   warps 0-3         epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
-//                     direct and mirrored global stores
+//                     M = 128, N = 256, K = 16, into one of two TMEM
+//                     accumulators (warp 1 allocates all 512 columns)
+//   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
+//                     direct and mirrored global stores, overlapping the
+//                     next tile's MMAs
 // K loop: 3 segments of ceil(n/64) chunks: (hi, hi), (hi, lo), (lo, hi).
 // Every mbarrier wait is bounded; on expiry the CTA records CSK_ETIMEOUT,
 // drains its own TMA loads (bounded), frees its TMEM and returns.
@@ -34,12 +35,13 @@ namespace csk {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int STAGES = 3;
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;          // 16 KB
-constexpr int B_BYTES = BN * BK * 2;          // 16 KB
+constexpr int B_BYTES = BN * BK * 2;          // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 128;
+constexpr int TMEM_COLS = 2 * BN;             // two accumulators: MMA and epilogue overlap
+constexpr int kGramThreads = 192;             // 6 warps: TMA, MMA, 4 x epilogue
 constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before giving up
 
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -136,6 +138,24 @@ constexpr uint32_t kIdesc = (1u << 4)                 // D format F32
                             | ((uint32_t)(BN >> 3) << 17)
                             | ((uint32_t)(BM >> 4) << 24);
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Tile order: row blocks are taken in groups of kGroupRows; inside a group the
+// tiles run column block by column block, so the CTAs working at the same
+// time share a few A panels and B panels in L2.  Tiles entirely below the
+// diagonal (no element with col >= row) are skipped.
+constexpr int kGroupRows = 16;
+
+__device__ __forceinline__ bool tile_at(int t, int nbi, int nbj, int* bi, int* bj) {
+    const int per_group = kGroupRows * nbj;
+    const int g = t / per_group, rem = t - g * per_group;
+    *bj = rem / kGroupRows;
+    *bi = g * kGroupRows + (rem - *bj * kGroupRows);
+    return *bi < nbi && (*bj * BN + BN - 1) >= (*bi * BM);
+}
+
 // ----------------------------------------------------------------- kernels
 __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_pad, int k_pad,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
@@ -150,31 +170,39 @@ __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_p
     }
 }
 
-__global__ void __launch_bounds__(128, 2)
-k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-          int d, int kchunks, float* __restrict__ G, int64_t ldg, csk_info* info) {
-    const int bi = blockIdx.y, bj = blockIdx.x;
-    if (bj < bi) return;                            // lower triangle: mirrored by (bj, bi)
+// Persistent: CTA b computes tiles b, b + grid, ...  Warp 0 / lane 0 loads
+// K chunks through a 4-stage TMA ring; warp 1 / lane 0 issues the MMAs into
+// one of two TMEM accumulators; warps 2-5 drain the other accumulator to
+// global memory, so a tile's epilogue overlaps the next tile's MMAs.
+// Element (r, c) is written, with its mirror (c, r), exactly when c >= r.
+__global__ void __launch_bounds__(kGramThreads, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ CUtensorMap map_lo_a,
+          const __grid_constant__ CUtensorMap map_hi_b, const __grid_constant__ CUtensorMap map_lo_b,
+          int d, int kchunks, int ntiles, int nbi, int nbj, float* __restrict__ G, int64_t ldg,
+          csk_info* info) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
-    // 1024-byte alignment for the 128B-swizzled tiles
     unsigned char* dsm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int fail_sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
+        for (int st = 0; st < STAGES; ++st) {
+            mbar_init(smem_u32(&full_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&acc_full[a]), 1);
+            mbar_init(smem_u32(&acc_empty[a]), 4);      // one arrival per epilogue warp
+        }
         fail_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 2) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
                      "r"(TMEM_COLS)
@@ -187,99 +215,141 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     const uint32_t tmem = tmem_base_sh;
     const int nch = 3 * kchunks;
 
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer
-        int issued = 0;
-        bool ok = true;
-        for (int c = 0; c < nch && ok; ++c) {
-            const int s = c % STAGES, r = c / STAGES;
-            if (r > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (r - 1) & 1)) { ok = false; break; }
-            const int seg = c / kchunks, kc = c - seg * kchunks;
-            const CUtensorMap* ma = seg == 2 ? &map_lo : &map_hi;
-            const CUtensorMap* mb = seg == 1 ? &map_lo : &map_hi;
-            const uint32_t sa = smem_u32(dsm + s * STAGE_BYTES);
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_2d(sa, ma, fb, kc * BK, bi * BM);
-            tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN);
-            issued = c + 1;
-        }
-        if (!ok) {
-            atomicExch(&fail_sh, 1);
-            // drain: wait (bounded) for the loads this thread issued
-            for (int c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
-                (void)mbar_wait(smem_u32(&full_bar[c % STAGES]), (c / STAGES) & 1);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        bool ok = true;
-        for (int c = 0; c < nch; ++c) {
-            const int s = c % STAGES, r = c / STAGES;
-            if (!mbar_wait(smem_u32(&full_bar[s]), r & 1)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(dsm + s * STAGE_BYTES);
-            const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                tc_mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
-                            (c > 0 || kk > 0) ? 1u : 0u);
-            tc_commit(smem_u32(&empty_bar[s]));    // stage free once these MMAs finish
-        }
-        if (ok) tc_commit(smem_u32(&acc_bar));     // accumulator complete
-        else atomicExch(&fail_sh, 1);
-    }
-    __syncwarp();
-
-    // ---- epilogue: every warp reads its 32 TMEM lanes (= tile rows)
-    const bool acc_ok = mbar_wait(smem_u32(&acc_bar), 0);
-    const int good = __syncthreads_and(acc_ok && !fail_sh);   // uniform over the CTA
-    tc_fence_after();
-    const int row = bi * BM + warp * 32 + lane;
-    const bool vec_ok = (ldg % 4 == 0) && (reinterpret_cast<uintptr_t>(G) % 16 == 0);
-    if (good) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            const int col0 = bj * BN + c0;
-            if (bj != bi) {
-                if (row < d) {
-                    float* dst = G + (int64_t)row * ldg + col0;
-                    if (vec_ok && col0 + 32 <= d) {
-#pragma unroll
-                        for (int q = 0; q < 32; q += 4)
-                            *reinterpret_cast<float4*>(dst + q) =
-                                make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
-                                            __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            if (col0 + q < d) dst[q] = __uint_as_float(v[q]);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            int64_t g = 0;                 // chunk counter over all tiles of this CTA
+            int64_t issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int bi, bj;
+                if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+                for (int c = 0; c < nch; ++c, ++g) {
+                    const int st = (int)(g % STAGES);
+                    const int64_t r = g / STAGES;
+                    if (r > 0 && !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((r - 1) & 1))) {
+                        ok = false;
+                        break;
                     }
+                    const int seg = c / kchunks, kc = c - seg * kchunks;
+                    const CUtensorMap* ma = seg == 2 ? &map_lo_a : &map_hi_a;
+                    const CUtensorMap* mb = seg == 1 ? &map_lo_b : &map_hi_b;
+                    const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
+                    const uint32_t fb = smem_u32(&full_bar[st]);
+                    mbar_expect_tx(fb, STAGE_BYTES);
+                    tma_load_2d(sa, ma, fb, kc * BK, bi * BM);
+                    tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN);
+                    issued = g + 1;
                 }
-                // mirrored tile: G[col][row] -- consecutive lanes, consecutive addresses
+            }
+            if (!ok) {
+                atomicExch(&fail_sh, 1);
+                for (int64_t q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+                    (void)mbar_wait(smem_u32(&full_bar[q % STAGES]), (uint32_t)((q / STAGES) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            int64_t g = 0;
+            int tc = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int bi, bj;
+                if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+                const int a = tc & 1, u = tc >> 1;
+                ++tc;
+                if (u > 0 && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)((u - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(a * BN);
+                for (int c = 0; c < nch; ++c, ++g) {
+                    const int st = (int)(g % STAGES);
+                    if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((g / STAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
+                    const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (col0 + q < d && row < d) G[(int64_t)(col0 + q) * ldg + row] = __uint_as_float(v[q]);
-            } else {
-                // diagonal tile: (r, c) and (c, r) are summed in different
-                // orders here, so keep the upper triangle and mirror it
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        tc_mma_bf16(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                    kIdesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    tc_commit(smem_u32(&empty_bar[st]));
+                }
+                if (ok) tc_commit(smem_u32(&acc_full[a]));
+            }
+            if (!ok) atomicExch(&fail_sh, 1);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31
+        const int quad = warp & 3;
+        const bool vec_ok = (ldg % 4 == 0) && (reinterpret_cast<uintptr_t>(G) % 16 == 0);
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int bi, bj;
+            if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+            const int a = tc & 1, u = tc >> 1;
+            ++tc;
+            const bool ok = mbar_wait(smem_u32(&acc_full[a]), (uint32_t)(u & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicExch(&fail_sh, 1);
+                break;
+            }
+            tc_fence_after();
+            const int row = bi * BM + quad * 32 + lane;
+            const bool upper = (bj * BN) >= (bi * BM + BM);     // every column > every row
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * BN + c0), v);
+                const int col0 = bj * BN + c0;
+                if (upper) {
+                    if (row < d) {
+                        float* dst = G + (int64_t)row * ldg + col0;
+                        // streaming stores: G is written once here and read much
+                        // later, so keep the BF16 operands resident in L2 instead
+                        if (vec_ok && col0 + 32 <= d) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int col = col0 + q;
-                    if (row < d && col < d && col >= row) {
-                        G[(int64_t)row * ldg + col] = __uint_as_float(v[q]);
-                        G[(int64_t)col * ldg + row] = __uint_as_float(v[q]);
+                            for (int q = 0; q < 32; q += 4)
+                                __stcs(reinterpret_cast<float4*>(dst + q),
+                                       make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                                   __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3])));
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 32; ++q)
+                                if (col0 + q < d) __stcs(dst + q, __uint_as_float(v[q]));
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (col0 + q < d && row < d)
+                            __stcs(G + (int64_t)(col0 + q) * ldg + row, __uint_as_float(v[q]));
+                } else {
+                    // tile on the diagonal band: (r, c) and (c, r) are summed in
+                    // different orders, so keep c >= r and mirror it
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int col = col0 + q;
+                        if (row < d && col < d && col >= row) {
+                            __stcs(G + (int64_t)row * ldg + col, __uint_as_float(v[q]));
+                            __stcs(G + (int64_t)col * ldg + row, __uint_as_float(v[q]));
+                        }
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
         }
-    } else if (threadIdx.x == 0 && info) {
-        set_status_once(info, CSK_ETIMEOUT);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 2) {
+    if (threadIdx.x == 0 && fail_sh && info) set_status_once(info, CSK_ETIMEOUT);
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS)
@@ -313,12 +383,12 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* map, void* base, int rows, int cols) {
+bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -330,26 +400,34 @@ bool make_map(CUtensorMap* map, void* base, int rows, int cols) {
 int64_t gram_ld(int d) { return round_up(d, 32); }
 
 size_t gram_scratch_bytes(int d, int n) {
-    const int64_t dp = round_up(d, BM), kp = round_up(n, BK);
+    const int64_t dp = round_up(d, BN), kp = round_up(n, BK);
     return (size_t)(2 * dp * kp * 2 + 1024);
 }
 
 cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* N2, float* G,
                                    int64_t ldg, void* scratch, csk_info* info, cudaStream_t st) {
-    const int dp = (int)round_up(d, BM), kp = (int)round_up(n, BK);
+    const int dp = (int)round_up(d, BN), kp = (int)round_up(n, BK);
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(scratch) + 1023) & ~uintptr_t(1023));
     __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base);
     __nv_bfloat16* lo = hi + (size_t)dp * kp;
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
     k_split_bf16<<<di.sms * 8, 256, 0, st>>>(At, d, n, dp, kp, hi, lo);
-    CUtensorMap mh, ml;
-    if (!make_map(&mh, hi, dp, kp) || !make_map(&ml, lo, dp, kp)) return cudaErrorInvalidValue;
+    CUtensorMap mha, mla, mhb, mlb;
+    if (!make_map(&mha, hi, dp, kp, BM) || !make_map(&mla, lo, dp, kp, BM) ||
+        !make_map(&mhb, hi, dp, kp, BN) || !make_map(&mlb, lo, dp, kp, BN))
+        return cudaErrorInvalidValue;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
     cudaError_t e = ensure_smem_attr((const void*)k_gram_tc, smem);
     if (e != cudaSuccess) return e;
-    const int nt = dp / BM;
-    k_gram_tc<<<dim3(nt, nt), 128, smem, st>>>(mh, ml, d, kp / BK, G, ldg, info);
+    const int nbi = dp / BM, nbj = dp / BN;
+    // tile slots of the grouped order (some below the diagonal, skipped)
+    const int ntiles = (nbi + kGroupRows - 1) / kGroupRows * kGroupRows * nbj;
+    int valid = 0;
+    for (int i = 0; i < nbi; ++i) valid += nbj - (i * BM) / BN;
+    const int grid = valid < di.sms ? valid : di.sms;
+    k_gram_tc<<<grid, kGramThreads, smem, st>>>(mha, mla, mhb, mlb, d, kp / BK, ntiles, nbi, nbj, G,
+                                                ldg, info);
     if (N2) k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
     note_launches(N2 ? 3 : 2);
     return cudaGetLastError();
