@@ -287,14 +287,11 @@ def main():
         e2e_ok &= rc == 0 and inf["rse"] <= TOL
     te = time.perf_counter() - te
 
-    if world > 1:
-        t = torch.tensor([ms, te], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, te = float(t[0]), float(t[1])
-        c = torch.tensor([launches, int(ok and e2e_ok)], device=dev, dtype=torch.int64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        launches, ok_ranks = int(c[0]), int(c[1])
-        ok = ok_ranks == world
+    from paper_2004_02480_gb300 import replicas
+    job = replicas.aggregate(ms * 1e-3, K, launches, ok, device=dev)
+    job_e2e = replicas.aggregate(te, E, 0, e2e_ok, device=dev)
+    ms, te, launches, ok, e2e_ok = (job["elapsed_s"] * 1e3, job_e2e["elapsed_s"], job["launches"],
+                                    job["ok"], job_e2e["ok"])
 
     if rank != 0:
         dist.destroy_process_group()
@@ -319,7 +316,7 @@ def main():
                "sample": f"{n_done} whole oracle solves of this workload (FP64 sketch + literal "
                          f"Algorithm 1, mean IT {np.mean(its):.1f}) in {dt:.1f} s"}
 
-    value = world * K / (ms * 1e-3)
+    value = job["throughput"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -342,7 +339,7 @@ def main():
                      "note": "algorithmic bytes = (IT+1) residual evaluations x (4dn + 4(d+2n)); "
                              "At stays on chip (registers or shared memory), so this is not DRAM "
                              "traffic; the loop is bound by the per-step exchange latency"},
-        "e2e": {"value": world * E / te, "unit": UNIT,
+        "e2e": {"value": job_e2e["throughput"], "unit": UNIT,
                 "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes + 4 * N_COLS),
                 "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok)},
         "gpu_launches": launches,

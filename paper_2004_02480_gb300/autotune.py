@@ -42,7 +42,7 @@ def _store(cache):
 
 
 def candidates(sms: int):
-    fr = [1.0, 0.9, 0.84, 0.75, 0.66, 0.5]
+    fr = [1.0, 0.9, 0.84, 0.75, 0.66, 0.6, 0.5]
     return sorted({max(1, int(round(sms * f))) for f in fr}, reverse=True)
 
 

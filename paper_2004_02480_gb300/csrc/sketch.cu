@@ -7,9 +7,10 @@
 //   k_scatter     perm_tmp: rows grouped by bucket (arbitrary order inside)
 //   k_bucket_sort perm: each bucket sorted by row index, i.e. the rows in
 //                 (h(i), i) order -- unique, so independent of atomic order
-//   k_segsum      At_j = sum_{p in bucket j, ascending} D_ii A_i, Bt likewise,
-//                 and ||At_j||^2 in FP64: one CTA per bucket, a warp per
-//                 128-column chunk, 128-bit loads, 4 rows in flight per warp.
+//   k_segsum      At_j = sum_{p in bucket j, ascending} D_ii A_i and ||At_j||^2
+//                 in FP64: one CTA per bucket, a warp per 128-column chunk,
+//                 128-bit loads, 4 rows in flight per warp
+//   k_segsum_b    Bt likewise (right-hand sides), one warp per bucket
 #include <climits>
 #include <cstdio>
 
@@ -298,10 +299,6 @@ k_segsum(const T* __restrict__ A, int64_t lda, int n, const T* __restrict__ B, i
         double sq = 0.0;
         for (int c0 = warp * CW; c0 < n; c0 += W * CW)
             sq += seg_chunk<T, V, CPL, U>(A, lda, n, c0, perm, p0, p1, seed, At + j * (int64_t)n);
-        if (warp == 0 && B && nrhs > 0)
-            for (int c0 = 0; c0 < nrhs; c0 += 64)
-                (void)seg_chunk<T, 1, 2, 4>(B, ldb, nrhs, c0, perm, p0, p1, seed,
-                                            Bt + j * (int64_t)nrhs);
         sq = warp_sum(sq);
         if (lane_id() == 0) part[warp] = sq;
         __syncthreads();
@@ -311,6 +308,37 @@ k_segsum(const T* __restrict__ A, int64_t lda, int n, const T* __restrict__ B, i
             N2[j] = t;
         }
         __syncthreads();
+    }
+}
+
+// Signed sums of the right-hand sides, one warp per bucket (grid-stride),
+// ascending row order.  One right-hand side: the lanes load 32 rows' values
+// at once and the sum takes them in order through shuffles, so the loads of
+// a bucket overlap while the order stays fixed.  Several: lanes run over the
+// columns, rows in order, 4 rows in flight.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __restrict__ perm,
+           const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ Bt) {
+    const int lane = lane_id();
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < d; j += nwarps) {
+        const int32_t p0 = off[j], p1 = off[j + 1];
+        if (nrhs == 1) {
+            T acc = T(0);
+            for (int32_t pb = p0; pb < p1; pb += 32) {
+                const bool valid = pb + lane < p1;
+                const int32_t row = valid ? perm[pb + lane] : 0;
+                T v = valid ? B[(int64_t)row * ldb] : T(0);
+                if (row_negative(row_hash(seed, (uint64_t)row))) v = -v;
+                const int cnt = min(32, p1 - pb);
+                for (int q = 0; q < cnt; ++q) acc += __shfl_sync(0xffffffffu, v, q);
+            }
+            if (lane == 0) Bt[j] = acc;
+        } else {
+            for (int c0 = 0; c0 < nrhs; c0 += 32)
+                (void)seg_chunk<T, 1, 1, 4>(B, ldb, nrhs, c0, perm, p0, p1, seed, Bt + j * (int64_t)nrhs);
+        }
     }
 }
 
@@ -424,6 +452,17 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int n, const vo
                 (double*)At, (double*)Bt, N2);
     }
     note_launches(1);
+    if (B && nrhs > 0) {
+        int64_t bblocks = ((int64_t)d + 7) / 8;
+        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
+        if (dtype == CSK_F32)
+            k_segsum_b<float><<<(int)bblocks, 256, 0, st>>>((const float*)B, ldb, nrhs, perm, off, d,
+                                                            seed, (float*)Bt);
+        else
+            k_segsum_b<double><<<(int)bblocks, 256, 0, st>>>((const double*)B, ldb, nrhs, perm, off,
+                                                             d, seed, (double*)Bt);
+        note_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -49,12 +49,61 @@ def request_bytes(r: Request) -> int:
     """Device bytes a request holds while admitted: A, B, X*, X, info, and its
     part of the batched workspace (sketch, B sketch, norms, Gram matrix, plus
     sort and operand scratch bounded by its own sizes)."""
-    f = 4
+    f, al = 4, 256
+    up = lambda v: (int(v) + al - 1) // al * al  # noqa: E731
     ldg = (r.d + 31) // 32 * 32
-    core = f * (r.m * r.n + r.m * r.nrhs + 2 * r.n * r.nrhs) + 64 * r.nrhs
-    sketch = f * (r.d * r.n + r.d * r.nrhs) + 8 * r.d + f * r.d * ldg
-    scratch = 4 * (2 * r.d + 2 * r.m) + 4 * (r.d + 127) // 128 * 128 * ((r.n + 63) // 64 * 64)
+    core = (up(f * r.m * r.n) + up(f * r.m * r.nrhs) + 2 * up(f * r.n * r.nrhs) + up(64 * r.nrhs))
+    sketch = up(f * r.d * r.n) + up(f * r.d * r.nrhs) + up(8 * r.d) + up(f * r.d * ldg)
+    dp, kp = (r.d + 255) // 256 * 256, (r.n + 63) // 64 * 64
+    scratch = up(4 * (2 * r.d + 2 * r.m + 2)) + up(4 * dp * kp) + 2048
     return int(core + sketch + scratch + 4096)
+
+
+class Arena:
+    """First-fit allocator of 256-byte aligned ranges in one preallocated
+    device buffer, with coalescing on release.  The serving loop carves every
+    per-request tensor from it, so steady-state serving makes no cudaMalloc /
+    cudaFree (which would synchronise the device) and the HBM budget is a
+    real reservation.  Plain Python; the buffer itself is any object the
+    caller slices (a torch uint8 tensor on the GPU)."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes: int):
+        self.size = int(nbytes) // self.ALIGN * self.ALIGN
+        self.free = [(0, self.size)]          # sorted, non-adjacent (offset, length)
+
+    def alloc(self, nbytes: int) -> int | None:
+        n = (int(nbytes) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        for i, (o, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (o + n, ln - n)
+                return o
+        return None
+
+    def release(self, off: int, nbytes: int):
+        n = (int(nbytes) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        lo, hi = 0, len(self.free)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if self.free[mid][0] < off:
+                lo = mid + 1
+            else:
+                hi = mid
+        self.free.insert(lo, (off, n))
+        # merge with the right and the left neighbour
+        if lo + 1 < len(self.free) and off + n == self.free[lo + 1][0]:
+            self.free[lo] = (off, n + self.free[lo + 1][1])
+            self.free.pop(lo + 1)
+        if lo > 0 and self.free[lo - 1][0] + self.free[lo - 1][1] == off:
+            self.free[lo - 1] = (self.free[lo - 1][0], self.free[lo - 1][1] + self.free[lo][1])
+            self.free.pop(lo)
+
+    def in_use(self) -> int:
+        return self.size - sum(ln for _, ln in self.free)
 
 
 class Admission:
@@ -89,6 +138,11 @@ class Admission:
             self.used -= request_bytes(r)
         assert self.used >= 0
 
+    def unadmit(self, group: list[Request]):
+        """Return an admitted group to the head of the queue, in order."""
+        self.release(group)
+        self.waiting.extendleft(reversed(group))
+
 
 def poisson_requests(rate: float, seconds: float, seed: int, m_range=(2000, 100000),
                      n_range=(20, 500), d_factor=8, rhs_range=(1, 16)) -> list[Request]:
@@ -117,42 +171,82 @@ class Server:
         self.torch, self.csk = torch, csk
         self.dev = torch.device(device)
         self.adm = Admission(budget_bytes, max_group)
+        # the whole budget is reserved once; requests are carved out of it
+        self.arena = Arena(int(budget_bytes))
+        self.pool = torch.empty(self.arena.size, dtype=torch.uint8, device=self.dev)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
         self.params = csk.csk_params_default(tol=tol, threads=threads)
         self.keep_x = keep_x
         self.launches = 0
+        self.gen = torch.Generator(device=self.dev)
 
-    def _materialise(self, r: Request):
+    def _take(self, nbytes: int, held: list):
+        off = self.arena.alloc(nbytes)
+        if off is None:
+            return None
+        held.append((off, nbytes))
+        return self.pool[off:off + ((nbytes + 3) // 4) * 4]
+
+    def _materialise(self, r: Request, held: list, info):
         """The request's data, generated on the device from its seed (stands in
-        for a request that arrives with its matrix)."""
+        for a request that arrives with its matrix), in arena memory."""
         torch = self.torch
-        g = torch.Generator(device=self.dev).manual_seed(r.seed & ((1 << 63) - 1))
-        A = torch.randn((r.m, r.n), generator=g, device=self.dev, dtype=torch.float32)
-        X = torch.randn((r.n, r.nrhs), generator=g, device=self.dev, dtype=torch.float32)
-        B = A @ X
-        return self.csk.BatchSystem(A=A, B=B, d=r.d, seed=r.seed, Xstar=X)
+        f32 = torch.float32
+        parts = [r.m * r.n * 4, r.m * r.nrhs * 4, r.n * r.nrhs * 4, r.n * r.nrhs * 4]
+        views = []
+        for nb in parts:
+            v = self._take(nb, held)
+            if v is None:
+                return None
+            views.append(v)
+        A = views[0].view(f32).view(r.m, r.n)
+        B = views[1].view(f32).view(r.m, r.nrhs)
+        X = views[2].view(f32).view(r.n, r.nrhs)
+        Xo = views[3].view(f32).view(r.n, r.nrhs)
+        g = self.gen
+        g.manual_seed(r.seed & ((1 << 63) - 1))
+        torch.randn((r.m, r.n), generator=g, device=self.dev, dtype=f32, out=A)
+        torch.randn((r.n, r.nrhs), generator=g, device=self.dev, dtype=f32, out=X)
+        torch.matmul(A, X, out=B)
+        return self.csk.BatchSystem(A=A, B=B, d=r.d, seed=r.seed, Xstar=X, Xout=Xo, info=info)
 
     def solve_group(self, group: list[Request], stream):
+        """Launch one group on `stream`; None (nothing held) if the arena is
+        too fragmented to place it right now."""
         torch = self.torch
+        held = []
         with torch.cuda.stream(stream):
-            systems = [self._materialise(r) for r in group]
-            # one info buffer per group, so retiring it is one device-to-host copy
-            info = torch.zeros((sum(r.nrhs for r in group), 64), dtype=torch.uint8, device=self.dev)
+            systems = []
+            # the group's info records sit together: one copy retires it
+            rows = sum(r.nrhs for r in group)
+            infos = self._take(64 * rows, held)
             o = 0
-            for r, y in zip(group, systems):
-                y.info = info[o:o + r.nrhs]
+            for r in group if infos is not None else ():
+                info = infos[64 * o:64 * (o + r.nrhs)].view(r.nrhs, 64)
                 o += r.nrhs
-            ws = torch.empty(max(self.csk.csk_solve_batched_workspace_size(systems), 256),
-                             dtype=torch.uint8, device=self.dev)
+                y = self._materialise(r, held, info)
+                if y is None:
+                    break
+                systems.append(y)
+            ws = None
+            if len(systems) == len(group):
+                ws = self._take(max(self.csk.csk_solve_batched_workspace_size(systems), 256), held)
+            if ws is None:
+                for off, nb in held:
+                    self.arena.release(off, nb)
+                return None
             self.csk.csk_solve_batched(systems, self.params, ws=ws, sync=False)
             self.launches += 1
             ev = torch.cuda.Event()
             ev.record(stream)
-        return (systems, info), ws, ev
+        return systems, held, ev
 
-    def _retire(self, group, systems_info, now):
-        systems, info = systems_info
-        recs = np.frombuffer(info.cpu().numpy().tobytes(), dtype=self.csk.INFO_DTYPE)
+    def _retire(self, group, systems, held, now):
+        # one device-to-host copy of every info record of the group (the
+        # first range taken by solve_group)
+        off, nb = held[0]
+        recs = np.frombuffer(self.pool[off:off + nb].cpu().numpy().tobytes(),
+                             dtype=self.csk.INFO_DTYPE)
         o = 0
         for r, y in zip(group, systems):
             rr = recs[o:o + r.nrhs]
@@ -162,15 +256,19 @@ class Server:
             r.iters = [int(v) for v in rr["iters"]]
             if self.keep_x:
                 r.x = y.Xout.cpu().numpy()
+        for off, nb in held:
+            self.arena.release(off, nb)
         t = now()
         for r in group:
             r.t_done = t
 
     def warm_up(self):
-        """One small untimed group: CUDA context, kernels and allocator warm."""
+        """One small untimed group: CUDA context, kernels and libraries warm."""
         r = Request(-1, 0.0, 4000, 32, 256, 2, 12345)
-        (systems, info), ws, ev = self.solve_group([r], self.streams[0])
+        systems, held, ev = self.solve_group([r], self.streams[0])
         ev.synchronize()
+        for off, nb in held:
+            self.arena.release(off, nb)
 
     def run(self, requests: list[Request]) -> dict:
         self.warm_up()
@@ -185,20 +283,26 @@ class Server:
                 self.adm.arrive(pending.popleft())
             still = []
             for item in inflight:
-                group, systems, ws, ev = item
+                group, systems, held, ev = item
                 if ev.query():
-                    self._retire(group, systems, now)
+                    self._retire(group, systems, held, now)
                     self.adm.release(group)
                 else:
                     still.append(item)
             inflight = still
             group = self.adm.admit()
+            launched = None
+            if group:
+                launched = self.solve_group(group, self.streams[k % len(self.streams)])
+                if launched is None:              # arena fragmented: retry after a retire
+                    self.adm.unadmit(group)
+                    group = []
             if group:
                 for r in group:
                     r.t_admit = now()
-                systems, ws, ev = self.solve_group(group, self.streams[k % len(self.streams)])
+                systems, held, ev = launched
                 k += 1
-                inflight.append((group, systems, ws, ev))
+                inflight.append((group, systems, held, ev))
             elif not inflight and pending:
                 time.sleep(max(0.0, min(1e-3, pending[0].arrival - now())))
             else:

@@ -243,3 +243,26 @@ def test_register_variant_small_and_timeout(csk, grid):
     x, info, _ = _solve(csk, s, 400, 9, grid=grid, gemv_variant=2, spin_limit=20000,
                         fault_inject=1)
     assert info["status"] == -3
+
+
+def test_bench_launch_configuration_matches_oracle(csk):
+    """The configuration bench.py times (autotuned CTA count and loop variant
+    on the 100000 x 500, d = 5000 workload) gives the oracle's row sequence up
+    to the first near-tie and valid steps throughout."""
+    from paper_2004_02480_gb300 import autotune
+    m, n, d, seed = 100000, 500, 5000, 0
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    A, b = _to(s.A), _to(s.b)
+    xs = _to(s.x_star.astype(np.float32))
+    p = csk.csk_params_default(d=d, seed=seed, path=csk.GEMV)
+    tuned = autotune.tune_solve(A, b, p, x_star=xs, use_cache=False)
+    x, info, ik, X = _solve(csk, s, d, seed, log=20000, xlog=20000, path=csk.GEMV,
+                            grid=tuned["grid"], gemv_variant=tuned["gemv_variant"])
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At32.astype(np.float64), bt32.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6 and info["grid"] == tuned["grid"]
+    _compare_prefix(ik, ref, 1e-3)
+    _check_steps(At32, bt32, X, ik, info["iters"] - 1, 2.0 ** -24)
+    assert abs(info["iters"] - ref.iters) <= 0.05 * ref.iters

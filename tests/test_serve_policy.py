@@ -66,3 +66,30 @@ def test_poisson_stream_statistics():
     assert all(r.d == 8 * r.n for r in reqs) and all(1 <= r.nrhs <= 16 for r in reqs)
     # log-uniform m: log(m) has the uniform mean
     assert abs(np.log(m).mean() - (np.log(2000) + np.log(100000)) / 2) < 0.05
+
+
+def test_arena_first_fit_and_coalescing():
+    from paper_2004_02480_gb300.serve import Arena
+    a = Arena(10 * 256)
+    x = a.alloc(256); y = a.alloc(300); z = a.alloc(256)
+    assert (x, y, z) == (0, 256, 768) and a.in_use() == 4 * 256
+    assert a.alloc(7 * 256) is None                 # only 6 blocks left
+    a.release(y, 300)
+    assert a.alloc(512) == 256                      # first fit reuses the hole
+    a.release(256, 512); a.release(x, 256); a.release(z, 256)
+    assert a.free == [(0, 10 * 256)] and a.in_use() == 0
+    rng = __import__("numpy").random.default_rng(0)
+    live = []
+    for _ in range(2000):
+        if live and rng.random() < 0.5:
+            o, n = live.pop(int(rng.integers(len(live))))
+            a.release(o, n)
+        else:
+            n = int(rng.integers(1, 1000))
+            o = a.alloc(n)
+            if o is not None:
+                live.append((o, n))
+        spans = sorted((o, (n + 255) // 256 * 256) for o, n in live)
+        for (o1, n1), (o2, _) in zip(spans, spans[1:]):
+            assert o1 + n1 <= o2                    # no overlap
+        assert a.in_use() == sum(n for _, n in spans)
