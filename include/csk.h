@@ -240,6 +240,44 @@ int csk_solve_host(const void *A_host, int64_t m, int64_t n, int64_t lda,
                    void *ws, size_t ws_bytes, void *stream);
 
 /* ----------------------------------------------------------------------
+ * csk_solve_host_many -- a sequence of csk_solve_host problems, solved one
+ * after another on `stream`, with the host-to-device copies of problem k+1
+ * (on a stream the call creates and destroys) overlapping the solve of
+ * problem k.  Every problem is an independent run of Algorithm 1 with the
+ * same params (one sketch seed, d, tolerance, path); overlapping the copies
+ * changes no arithmetic.  This is the pipelining a solver service applies
+ * to a stream of systems arriving in host memory (the paper has no
+ * counterpart: it concerns one solve).
+ * probs   host array of `count` problems; every pointer in it is HOST memory
+ *         (page-locked for the copies to overlap; pageable works but
+ *         serialises more); A m x n with leading dimension lda, x0 / x_star
+ *         nullable, x_out n elements, info one record.  The results of
+ *         problem k are queued after the input copies of problem k+1.
+ * ws      DEVICE scratch of csk_solve_host_many_workspace_size(...) bytes:
+ *         two staging areas (the largest problem's device copies) that
+ *         alternate, plus one csk_solve workspace shared by the solves.
+ * Returns after every queued solve has finished: CSK_OK, the first
+ * non-OK solve status in problem order (each info record holds its own),
+ * or an argument / CUDA error.  The argument checks of every problem run
+ * before any copy is queued; count == 0 does nothing.
+ * -------------------------------------------------------------------- */
+typedef struct {
+    const void *A;        /* m x n, leading dimension lda (host)                */
+    int64_t m, n, lda;
+    const void *b;        /* m (host)                                           */
+    const void *x0;       /* nullable, n (host)                                 */
+    const void *x_star;   /* nullable, n (host)                                 */
+    void *x_out;          /* out, n (host)                                      */
+    csk_info *info;       /* out, one record (host)                             */
+} csk_host_problem;
+
+size_t csk_solve_host_many_workspace_size(const csk_host_problem *probs, int32_t count,
+                                          int32_t dtype, const csk_params *params);
+
+int csk_solve_host_many(const csk_host_problem *probs, int32_t count, int32_t dtype,
+                        const csk_params *params, void *ws, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------------
  * csk_solve_batched -- many independent systems, each with several
  * right-hand sides, in one persistent launch (FP32, GRAM residual path).
  *

@@ -62,6 +62,12 @@ INFO_DTYPE = np.dtype([("status", "<i4"), ("path", "<i4"), ("iters", "<i8"), ("r
 assert INFO_DTYPE.itemsize == 64
 
 
+class csk_host_problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("b", ctypes.c_void_p), ("x0", ctypes.c_void_p),
+                ("x_star", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+
+
 def lib():
     """Load libcsk.so (raises if it has not been built)."""
     global _lib
@@ -106,6 +112,12 @@ def lib():
         L.csk_solve_host.argtypes = [P, i64, i64, i64, P, i32, ctypes.POINTER(csk_params), P, P,
                                      P, P, P, sz, P]
         L.csk_solve_host.restype = ctypes.c_int
+        L.csk_solve_host_many_workspace_size.argtypes = [ctypes.POINTER(csk_host_problem), i32, i32,
+                                                         ctypes.POINTER(csk_params)]
+        L.csk_solve_host_many_workspace_size.restype = sz
+        L.csk_solve_host_many.argtypes = [ctypes.POINTER(csk_host_problem), i32, i32,
+                                          ctypes.POINTER(csk_params), P, sz, P]
+        L.csk_solve_host_many.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -331,6 +343,69 @@ def csk_solve_host(A: np.ndarray, b: np.ndarray, params: csk_params, x0=None, x_
         raise CskError(rc, "csk_solve_host")
     rec = info[0]
     return x_out, {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}, rc
+
+
+@dataclass
+class HostProblem:
+    """One problem of csk_solve_host_many (host numpy arrays, ideally
+    page-locked).  x_out / info are filled by the call."""
+    A: np.ndarray
+    b: np.ndarray
+    x0: np.ndarray | None = None
+    x_star: np.ndarray | None = None
+    x_out: np.ndarray | None = None
+    info: np.ndarray | None = None
+
+
+def _host_problems(probs: list[HostProblem]):
+    dt = None
+    arr = (csk_host_problem * max(1, len(probs)))()
+    for i, q in enumerate(probs):
+        A = q.A
+        if A.ndim != 2 or A.strides[1] != A.itemsize:
+            raise ValueError("A must be 2-D row-major")
+        t = CSK_F32 if A.dtype == np.float32 else CSK_F64 if A.dtype == np.float64 else None
+        if t is None or (dt is not None and t != dt):
+            raise TypeError("every A must be float32, or every A float64")
+        dt = t
+        for v in (q.b, q.x0, q.x_star):
+            if v is not None and (v.dtype != A.dtype or not v.flags.c_contiguous):
+                raise TypeError("b, x0, x_star must be contiguous with A's dtype")
+        m, n = A.shape
+        if q.x_out is None:                          # page-locked, so results copy back
+            q.x_out = torch.empty(n, dtype=torch.float32 if t == CSK_F32 else torch.float64
+                                  ).pin_memory().numpy()
+        if q.info is None:
+            q.info = torch.zeros(INFO_DTYPE.itemsize, dtype=torch.uint8).pin_memory().numpy(
+            ).view(INFO_DTYPE)
+        hp = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        arr[i] = csk_host_problem(hp(A), m, n, A.strides[0] // A.itemsize, hp(q.b), hp(q.x0),
+                                  hp(q.x_star), hp(q.x_out), hp(q.info))
+    return arr, (dt if dt is not None else CSK_F32)
+
+
+def csk_solve_host_many_workspace_size(probs: list[HostProblem], params: csk_params) -> int:
+    arr, dt = _host_problems(probs)
+    return int(lib().csk_solve_host_many_workspace_size(arr, len(probs), dt, ctypes.byref(params)))
+
+
+def csk_solve_host_many(probs: list[HostProblem], params: csk_params, *, ws: torch.Tensor,
+                        device=None) -> int:
+    """Solve every problem of ``probs`` (host memory) in order, the copies of
+    the next one overlapping the current solve.  Fills each problem's x_out
+    and info; returns the call's status (first non-OK solve status, else 0)."""
+    arr, dt = _host_problems(probs)
+    dev = ws.device if device is None else device
+    rc = lib().csk_solve_host_many(arr, len(probs), dt, ctypes.byref(params), _ptr(ws), ws.numel(),
+                                   _stream(dev))
+    if rc < 0 and not any(q.info is not None and q.info["status"][0] == rc for q in probs):
+        raise CskError(rc, "csk_solve_host_many")
+    return rc
+
+
+def info_dict(info: np.ndarray) -> dict:
+    rec = info[0]
+    return {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}
 
 
 def csk_sketch_noalloc(A: torch.Tensor, d: int, seed: int, b: torch.Tensor | None = None, *,

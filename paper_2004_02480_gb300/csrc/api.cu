@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libcsk (include/csk.h): argument checks, workspace
 // layout and the stream-ordered launch sequence of each entry point.
+#include <algorithm>
 #include <atomic>
 #include <climits>
 #include <cmath>
@@ -116,6 +117,23 @@ void host_staging(int64_t m, int64_t n, int dtype, HostStaging* H) {
     H->x = o;    o += align256((size_t)n * s);
     H->info = o; o += 256;
     H->total = o;
+}
+
+// Host-to-device copies of one csk_solve_host problem; A is packed to leading
+// dimension n on the device (one linear copy when it already is).
+cudaError_t copy_in(const void* A_host, int64_t m, int64_t n, int64_t lda, const void* b_host,
+                    const void* x0_host, const void* xs_host, size_t s, void* A, void* b,
+                    void* x0, void* xs, cudaStream_t st) {
+    cudaError_t e = lda == n
+        ? cudaMemcpyAsync(A, A_host, (size_t)m * n * s, cudaMemcpyHostToDevice, st)
+        : cudaMemcpy2DAsync(A, (size_t)n * s, A_host, (size_t)lda * s, (size_t)n * s, (size_t)m,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b, b_host, (size_t)m * s, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && x0)
+        e = cudaMemcpyAsync(x0, x0_host, (size_t)n * s, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && xs)
+        e = cudaMemcpyAsync(xs, xs_host, (size_t)n * s, cudaMemcpyHostToDevice, st);
+    return e;
 }
 
 inline void record(const csk_params* p, int i, cudaStream_t st) {
@@ -402,18 +420,122 @@ int csk_solve_host(const void* A_host, int64_t m, int64_t n, int64_t lda, const 
     void* xs = x_star_host ? w + H.xs : nullptr;
     void* x = w + H.x;
     csk_info* info = reinterpret_cast<csk_info*>(w + H.info);
-    // A is packed to leading dimension n on the device
-    CSK_CUDA_TRY(cudaMemcpy2DAsync(A, (size_t)n * s, A_host, (size_t)lda * s, (size_t)n * s,
-                                   (size_t)m, cudaMemcpyHostToDevice, st));
-    CSK_CUDA_TRY(cudaMemcpyAsync(b, b_host, (size_t)m * s, cudaMemcpyHostToDevice, st));
-    if (x0) CSK_CUDA_TRY(cudaMemcpyAsync(x0, x0_host, (size_t)n * s, cudaMemcpyHostToDevice, st));
-    if (xs) CSK_CUDA_TRY(cudaMemcpyAsync(xs, x_star_host, (size_t)n * s, cudaMemcpyHostToDevice, st));
+    CSK_CUDA_TRY(copy_in(A_host, m, n, lda, b_host, x0_host, x_star_host, s, A, b, x0, xs, st));
     rc = solve_enqueue(A, m, n, n, b, dtype, params, x0, xs, x, info, w + H.total, L, st);
     if (rc != CSK_OK) return rc;
     CSK_CUDA_TRY(cudaMemcpyAsync(x_out_host, x, (size_t)n * s, cudaMemcpyDeviceToHost, st));
     CSK_CUDA_TRY(cudaMemcpyAsync(info_host, info, sizeof(csk_info), cudaMemcpyDeviceToHost, st));
     CSK_CUDA_TRY(cudaStreamSynchronize(st));
     return info_host->status;
+}
+
+size_t csk_solve_host_many_workspace_size(const csk_host_problem* probs, int32_t count,
+                                          int32_t dtype, const csk_params* params) {
+    if (!probs || count < 1 || !params) return 0;
+    size_t stage = 0, inner = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const size_t i = csk_solve_workspace_size(probs[k].m, probs[k].n, dtype, params);
+        if (i == 0) return 0;
+        HostStaging H;
+        host_staging(probs[k].m, probs[k].n, dtype, &H);
+        stage = std::max(stage, H.total);
+        inner = std::max(inner, i);
+    }
+    return 2 * stage + inner;
+}
+
+int csk_solve_host_many(const csk_host_problem* probs, int32_t count, int32_t dtype,
+                        const csk_params* params, void* ws, size_t ws_bytes, void* stream) {
+    if (count == 0) return CSK_OK;
+    if (!probs || count < 0 || !params || !ws) return CSK_EINVAL;
+    size_t stage = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const csk_host_problem& q = probs[k];
+        if (!q.A || !q.b || !q.x_out || !q.info) return CSK_EINVAL;
+        int rc = check_solve_args(q.m, q.n, q.lda, dtype, params, ws);
+        if (rc != CSK_OK) return rc;
+        HostStaging H;
+        host_staging(q.m, q.n, dtype, &H);
+        stage = std::max(stage, H.total);
+    }
+    if (ws_bytes < csk_solve_host_many_workspace_size(probs, count, dtype, params))
+        return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    const size_t s = dtype == CSK_F64 ? 8 : 4;
+    char* w = static_cast<char*>(ws);
+    char* inner = w + 2 * stage;
+
+    // copies of problem k+1 run on `cp` while problem k is solved on `st`;
+    // staging area k % 2 is reused once the solve that read it has finished
+    cudaStream_t cp = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    cudaError_t e = cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
+    }
+    int first_bad = CSK_OK;
+    // the copy stream starts after the work already queued on `st`
+    if (e == cudaSuccess) e = cudaEventRecord(freed[0], st);
+    if (e == cudaSuccess) e = cudaEventRecord(freed[1], st);
+    auto slot_at = [&](int32_t k, HostStaging* H) {
+        host_staging(probs[k].m, probs[k].n, dtype, H);
+        return w + (k & 1) * stage;
+    };
+    // results of problem k go back after the copies of k+1 are queued: a
+    // copy into pageable host memory holds the host until it is done, and
+    // must not hold back the next problem's input copies
+    auto queue_out = [&](int32_t k) {
+        HostStaging H;
+        char* sw = slot_at(k, &H);
+        cudaError_t r = cudaMemcpyAsync(probs[k].x_out, sw + H.x, (size_t)probs[k].n * s,
+                                        cudaMemcpyDeviceToHost, st);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(probs[k].info, sw + H.info, sizeof(csk_info),
+                                cudaMemcpyDeviceToHost, st);
+        if (r == cudaSuccess) r = cudaEventRecord(freed[k & 1], st);
+        return r;
+    };
+    int32_t solved = 0;
+    for (int32_t k = 0; k < count && e == cudaSuccess; ++k) {
+        const csk_host_problem& q = probs[k];
+        const int slot = k & 1;
+        HostStaging H;
+        char* sw = slot_at(k, &H);
+        void* A = sw + H.A;
+        void* b = sw + H.b;
+        void* x0 = q.x0 ? sw + H.x0 : nullptr;
+        void* xs = q.x_star ? sw + H.xs : nullptr;
+        csk_info* info = reinterpret_cast<csk_info*>(sw + H.info);
+        e = cudaStreamWaitEvent(cp, freed[slot], 0);
+        if (e == cudaSuccess) e = copy_in(q.A, q.m, q.n, q.lda, q.b, q.x0, q.x_star, s, A, b, x0, xs, cp);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[slot], cp);
+        if (e == cudaSuccess && k > 0) e = queue_out(k - 1);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, copied[slot], 0);
+        if (e != cudaSuccess) break;
+        SolveLayout L;
+        solve_layout(q.m, q.n, dtype, params->d, resolve_path(params->path, dtype, params->d, q.n), &L);
+        first_bad = solve_enqueue(A, q.m, q.n, q.n, b, dtype, params, x0, xs, sw + H.x, info, inner,
+                                  L, st);
+        if (first_bad != CSK_OK) break;
+        solved = k + 1;
+    }
+    if (e == cudaSuccess && first_bad == CSK_OK && solved == count) e = queue_out(count - 1);
+    // drain both streams before the events and the copy stream go away
+    const cudaError_t e1 = cudaStreamSynchronize(cp);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    for (int i = 0; i < 2; ++i) {
+        if (copied[i]) cudaEventDestroy(copied[i]);
+        if (freed[i]) cudaEventDestroy(freed[i]);
+    }
+    if (cp) cudaStreamDestroy(cp);
+    if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) return CSK_ECUDA;
+    if (first_bad != CSK_OK) return first_bad;
+    for (int32_t k = 0; k < count; ++k)
+        if (probs[k].info->status != CSK_OK) return probs[k].info->status;
+    return CSK_OK;
 }
 
 }  // extern "C"

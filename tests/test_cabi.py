@@ -106,3 +106,29 @@ def test_binding_refuses_cpu_tensors():
     torch = pytest.importorskip("torch")
     with pytest.raises(ValueError):
         csk.csk_sketch(torch.zeros(4, 2), 2, 0)
+
+
+def test_host_many_checks_on_host(L):
+    """csk_solve_host_many validates every problem before it touches CUDA."""
+    import numpy as np
+    p = csk.csk_params_default(d=8)
+    A = np.zeros((40, 4), np.float32)
+    b = np.zeros(40, np.float32)
+    out = dict(x_out=np.zeros(5, np.float32), info=np.zeros(1, csk.INFO_DTYPE))
+    probs = [csk.HostProblem(A=A, b=b, **out),
+             csk.HostProblem(A=np.zeros((60, 5), np.float32), b=np.zeros(60, np.float32), **out)]
+    arr, dt = csk._host_problems(probs)
+    one = csk.csk_solve_workspace_size(60, 5, csk.CSK_F32, p)
+    need = L.csk_solve_host_many_workspace_size(arr, 2, dt, ctypes.byref(p))
+    assert need > one > 0
+    assert L.csk_solve_host_many_workspace_size(arr, 0, dt, ctypes.byref(p)) == 0
+    fake = ctypes.c_void_p(256)
+    assert L.csk_solve_host_many(arr, 0, dt, ctypes.byref(p), fake, need, None) == csk.CSK_OK
+    assert L.csk_solve_host_many(arr, -1, dt, ctypes.byref(p), fake, need, None) == csk.CSK_EINVAL
+    assert L.csk_solve_host_many(arr, 2, dt, ctypes.byref(p), fake, need - 256, None) == csk.CSK_EINVAL
+    assert L.csk_solve_host_many(arr, 2, dt, None, fake, need, None) == csk.CSK_EINVAL
+    arr[1].lda = 3                                  # lda < n
+    assert L.csk_solve_host_many(arr, 2, dt, ctypes.byref(p), fake, need, None) == csk.CSK_EINVAL
+    arr[1].lda = 5
+    arr[0].b = None
+    assert L.csk_solve_host_many(arr, 2, dt, ctypes.byref(p), fake, need, None) == csk.CSK_EINVAL
