@@ -288,6 +288,24 @@ def main():
     te = time.perf_counter() - te
     e2e_ok = rc == 0 and all(csk.info_dict(q.info)["rse"] <= TOL for q in probs)
 
+    # the paper's comparison: MWRK on A itself (Remark 1, d = 0), same system;
+    # each step reads all of A (200 MB, larger than L2) from HBM
+    pm = csk.csk_params_default(d=0, tol=TOL, path=csk.GEMV)
+    wsm = csk._workspace(csk.csk_solve_workspace_size(M, N_COLS, csk.CSK_F32, pm), dev)
+    csk.csk_solve(A, b, pm, x_star=xs, ws=wsm)
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    RM = 2
+    m0.record()
+    for _ in range(RM):
+        _, inf_m = csk.csk_solve(A, b, pm, x_star=xs, ws=wsm, sync=False)
+    m1.record()
+    torch.cuda.synchronize()
+    inf_m = csk.read_info(inf_m)
+    mwrk = {"ms": m0.elapsed_time(m1) / RM, "iters": inf_m["iters"], "rse": inf_m["rse"],
+            "status": inf_m["status"]}
+    del wsm
+
     from paper_2004_02480_gb300 import replicas
     job = replicas.aggregate(ms * 1e-3, K, launches, ok, device=dev)
     job_e2e = replicas.aggregate(te, E, 0, e2e_ok, device=dev)
@@ -345,6 +363,10 @@ def main():
                 "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok),
                 "call": f"csk_solve_host_many over {E} solves from page-locked host memory "
                         "(the copies of solve k+1 overlap solve k)"},
+        "comparison": {"mwrk_unsketched_ms": mwrk["ms"], "mwrk_iters": mwrk["iters"],
+                       "mwrk_rse": mwrk["rse"], "mwrk_status": mwrk["status"],
+                       "csk_ms": ms / K, "csk_speedup_over_mwrk": mwrk["ms"] / (ms / K),
+                       "note": "MWRK (d = 0) on the same A, b on the GPU, 2 runs; not part of the timed steps"},
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -86,8 +86,13 @@ typedef struct {
     int64_t x_log_len;
     int32_t threads;        /* csk_solve_batched: threads per CTA, 0 = choice    */
     int32_t gemv_variant;   /* GEMV loop: 0 = library choice, 1 = rows of At in
-                               shared memory, 2 = rows of At in registers (FP32,
-                               n <= 512, n % 4 == 0, few rows per CTA)          */
+                               shared memory (or read from global memory when
+                               they do not fit), 2 = rows of At in registers
+                               (FP32, n <= 512, n % 4 == 0, few rows per CTA),
+                               3 = rows streamed every step through a shared-
+                               memory ring of bulk copies (FP32, n <= 1024,
+                               n % 4 == 0; the choice when rows fit neither
+                               registers nor shared memory)                     */
     void *stage_events[5];  /* optional cudaEvent_t handles (caller-owned), each
                                recorded on the stream when non-NULL: [0] before
                                the sketch, [1] after sketch and row norms, [2]

@@ -94,7 +94,7 @@ int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk
     if (params->x_log_len < 0 || (params->x_log_len > 0 && !params->x_log)) return CSK_EINVAL;
     if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_AUTO) return CSK_EINVAL;
     if (params->grid < 0 || params->refresh_every < 0) return CSK_EINVAL;
-    if (params->gemv_variant < 0 || params->gemv_variant > 2) return CSK_EINVAL;
+    if (params->gemv_variant < 0 || params->gemv_variant > 3) return CSK_EINVAL;
     if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
     const int path = resolve_path(params->path, dtype, d, n);

@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -47,32 +48,9 @@ constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before giving up
 inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 // ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false when the limit ran out.
+// (mbarrier helpers: async.cuh)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    return csk::mbar_wait(bar, parity, kWaitLimit);
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int c0, int c1) {
@@ -131,16 +109,12 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B, FP32 D,
-// both K-major, M = 128, N = 128.
+// both K-major, M = 128, N = 256.
 constexpr uint32_t kIdesc = (1u << 4)                 // D format F32
                             | (1u << 7)               // A format BF16
                             | (1u << 10)              // B format BF16
                             | ((uint32_t)(BN >> 3) << 17)
                             | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 // Tile order: row blocks are taken in groups of kGroupRows; inside a group the
 // tiles run column block by column block, so the CTAs working at the same
@@ -199,7 +173,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             mbar_init(smem_u32(&acc_empty[a]), 4);      // one arrival per epilogue warp
         }
         fail_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_fence_init();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {

@@ -29,6 +29,7 @@
 #include <climits>
 #include <cmath>
 
+#include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -543,6 +544,251 @@ bool reg_shape(int rows_per_cta, int n, int* rpw, int* cpl) {
     return false;
 }
 
+// ------------------------------------------------ GEMV path, streamed rows
+// FP32 variant for rows that fit neither registers nor shared memory (MWRK on
+// A itself, Remark 1, or a large sketch).  Every step streams the CTA's rows
+// from HBM through a ring of up to kMaxStreamStages shared-memory blocks of
+// kWarps * RPB rows, each filled by bulk copies (TMA, cp.async.bulk) that
+// complete on the block's `full` mbarrier; the eight warps release a block on
+// its `empty` mbarrier.  Thread 0 refills a stage one block after the CTA
+// left it (no producer warp, so the CTA barriers of the reduction and the
+// exchange see every thread), and tops the ring up before each exchange: the
+// rows are the same every step, so the next step's first blocks load while
+// this step's exchange runs.  Warp w scores rows w, w + kWarps, ... of each
+// block against its register copy of x (lane l holds float4 columns l,
+// l + 32, ...) with the register variant's arithmetic, order included, so
+// the two give identical iterates.  Needs n % 4 == 0, n <= 128 * CPL, a
+// leading dimension that is a multiple of 4 floats and 16-byte aligned rows.
+#ifndef CSK_STREAM_MAX_STAGES
+#define CSK_STREAM_MAX_STAGES 8
+#endif
+constexpr int kMaxStreamStages = CSK_STREAM_MAX_STAGES;   // ring depth: as many as fit, up to this
+constexpr uint32_t kStreamWait = 1u << 24;      // try_wait polls per bulk-copy wait
+
+template <int CPL>
+struct StreamShape {
+    static constexpr int RPB = CPL <= 2 ? 4 : 8 / CPL;   // rows per warp per block
+    static constexpr int ROWS = kWarps * RPB;            // rows per block (<= 32 KB)
+};
+
+size_t stream_smem_bytes(int R, int n, int rows_per_blk, int stages) {
+    return (size_t)stages * rows_per_blk * n * 4 + (size_t)2 * ((R + 3) & ~3) * 4;
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_iterate_gemv_stream(IterProblem p, int R, int nst) {
+    constexpr int RPB = StreamShape<CPL>::RPB, SR = StreamShape<CPL>::ROWS;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ RedShared<float> sh;
+    __shared__ __align__(8) uint64_t full[kMaxStreamStages];
+    __shared__ __align__(8) uint64_t empty[kMaxStreamStages];
+    int par = 0;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int n = p.n, d = p.d, n4 = n >> 2;
+    const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
+    const int nblk = (nr + SR - 1) / SR;
+    const size_t blk_floats = (size_t)SR * n;
+    float* ring = reinterpret_cast<float*>(dsm);
+    float* bts = ring + nst * blk_floats;
+    float* w2s = bts + ((R + 3) & ~3);
+    const float* At = static_cast<const float*>(p.At);
+    const float* bt = static_cast<const float*>(p.bt);
+    const float* x0 = static_cast<const float*>(p.x0);
+    const float* xstar = static_cast<const float*>(p.xstar);
+    const bool stat_owner = (b == 0 && warp == 0);
+    const bool packed = p.ld == n;
+
+    for (int q = tid; q < nr; q += blockDim.x) {
+        bts[q] = bt[r0 + q];
+        w2s[q] = weight_of<float>(p.N2[r0 + q]);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), kWarps);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // Thread 0 only: blocks issued so far (block g holds row block g % nblk
+    // in stage g % nst), and the stage, lap parity and row block of the next
+    // issue; refill(upto) issues up to block `upto`, each stage taken over
+    // once the warps released the block it held.
+    int64_t issued = 0;
+    int is = 0, iblk = 0;
+    uint32_t ilap = 0;
+    auto refill = [&](int64_t upto) -> bool {
+        for (; issued < upto; ++issued) {
+            if (issued >= nst && !mbar_wait(smem_u32(&empty[is]), ilap ^ 1u, kStreamWait))
+                return false;
+            const int q0 = iblk * SR, rows = min(SR, nr - q0);
+            const uint32_t bar = smem_u32(&full[is]);
+            const uint32_t dst = smem_u32(ring + is * blk_floats);
+            mbar_expect_tx(bar, (uint32_t)rows * n * 4);
+            if (packed) {
+                bulk_g2s(dst, At + (int64_t)(r0 + q0) * n, (uint32_t)rows * n * 4, bar);
+            } else {
+                for (int q = 0; q < rows; ++q)
+                    bulk_g2s(dst + (uint32_t)q * n * 4, At + (int64_t)(r0 + q0 + q) * p.ld,
+                             (uint32_t)n * 4, bar);
+            }
+            if (++iblk == nblk) iblk = 0;
+            if (++is == nst) { is = 0; ilap ^= 1u; }
+        }
+        return true;
+    };
+    int stalled = 0;
+    if (tid == 0 && nblk > 0 && !refill(nst)) stalled = 1;
+
+    float4 xr[CPL], xsr[CPL];
+#pragma unroll
+    for (int i = 0; i < CPL; ++i) {
+        const int c4 = lane + 32 * i;
+        xr[i] = (x0 && c4 < n4) ? reinterpret_cast<const float4*>(x0)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xsr[i] = (xstar && c4 < n4) ? reinterpret_cast<const float4*>(xstar)[c4]
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float threshold = (float)(p.tol * *p.stop_norm);
+    const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    uint32_t round = 0;
+    int64_t k = 0, g = 0;          // g: blocks consumed (the same count in every warp)
+    int cs = 0;                    // stage of block g and its lap parity
+    uint32_t clap = 0;
+    int status = CSK_OK;
+    for (;;) {
+        Red<float> c;
+        c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
+        for (int blk = 0; blk < nblk && !stalled; ++blk, ++g) {
+            const int s = cs;
+            const uint32_t lap = clap;
+            if (++cs == nst) { cs = 0; clap ^= 1u; }
+            if (!mbar_wait(smem_u32(&full[s]), lap, kStreamWait)) {
+                stalled = 1;
+                break;
+            }
+            const float* rows = ring + s * blk_floats;
+            const int q0 = blk * SR;
+            float dot[RPB];
+#pragma unroll
+            for (int u = 0; u < RPB; ++u) {
+                const float4* row = reinterpret_cast<const float4*>(rows + (size_t)(warp + kWarps * u) * n);
+                const bool live = q0 + warp + kWarps * u < nr;
+                float acc = 0.0f;
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int c4 = lane + 32 * i;
+                    if (live && c4 < n4) {
+                        const float4 a = row[c4];
+                        acc = fmaf(a.x, xr[i].x, acc);
+                        acc = fmaf(a.y, xr[i].y, acc);
+                        acc = fmaf(a.z, xr[i].z, acc);
+                        acc = fmaf(a.w, xr[i].w, acc);
+                    }
+                }
+                dot[u] = acc;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+            warp_sum_rows<RPB>(dot);
+#pragma unroll
+            for (int u = 0; u < RPB; ++u) {
+                const int q = q0 + warp + kWarps * u;
+                if (q < nr) {
+                    const float r = bts[q] - dot[u];
+                    const float w = w2s[q];
+                    if (!(w < 0.0f)) {
+                        const float key = r * r * w;
+                        if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
+                    }
+                    if (!xstar && lane == 0) c.stat += r * r;
+                }
+            }
+            // take over the stage of the previous block (released by now, as a rule)
+            if (tid == 0 && !refill(g + nst)) stalled = 1;
+        }
+        // top the ring up: the next step's first blocks load during the exchange
+        if (tid == 0 && nblk > 0 && !stalled && !refill(g + nst)) stalled = 1;
+        if (__syncthreads_or(stalled)) {
+            if (tid == 0) set_status_once(p.info, CSK_ETIMEOUT);
+            status = CSK_ETIMEOUT;
+            break;
+        }
+        if (xstar && warp == 0) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
+                    const float ex = xr[i].x - xsr[i].x, ey = xr[i].y - xsr[i].y;
+                    const float ez = xr[i].z - xsr[i].z, ew = xr[i].w - xsr[i].w;
+                    c.stat += ex * ex + ey * ey + ez * ez + ew * ew;
+                }
+            }
+        }
+        c = block_reduce_wu(c, sh, par);
+        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
+            status = CSK_ETIMEOUT;
+            break;
+        }
+        ++round;
+        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
+        if (dec != INT_MIN) { status = dec; break; }
+        if (stat_owner && lane == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
+        if (stat_owner && p.x_log && k < p.x_log_len)
+#pragma unroll
+            for (int i = 0; i < CPL; ++i)
+                if (lane + 32 * i < n4)
+                    reinterpret_cast<float4*>(static_cast<float*>(p.x_log) + k * n)[lane + 32 * i] = xr[i];
+        const float4* arow = reinterpret_cast<const float4*>(At + (int64_t)c.idx * p.ld);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int c4 = lane + 32 * i;
+            if (c4 < n4) {
+                const float4 v = __ldg(arow + c4);
+                xr[i].x = fmaf(c.alpha, v.x, xr[i].x);
+                xr[i].y = fmaf(c.alpha, v.y, xr[i].y);
+                xr[i].z = fmaf(c.alpha, v.z, xr[i].z);
+                xr[i].w = fmaf(c.alpha, v.w, xr[i].w);
+            }
+        }
+        ++k;
+    }
+    // no bulk copy may still be writing shared memory when the CTA exits
+    if (tid == 0)
+        for (int64_t q = g; q < issued; ++q) {
+            (void)mbar_wait(smem_u32(&full[cs]), clap, kStreamWait);
+            if (++cs == nst) { cs = 0; clap ^= 1u; }
+        }
+    if (stat_owner) {
+        float4* xo = reinterpret_cast<float4*>(p.x_out);
+#pragma unroll
+        for (int i = 0; i < CPL; ++i)
+            if (lane + 32 * i < n4) xo[lane + 32 * i] = xr[i];
+    }
+    finish(p.info, status, k);
+}
+
+const void* stream_kernel(int cpl) {
+    switch (cpl) {
+        case 1: return (const void*)k_iterate_gemv_stream<1>;
+        case 2: return (const void*)k_iterate_gemv_stream<2>;
+        case 4: return (const void*)k_iterate_gemv_stream<4>;
+        case 8: return (const void*)k_iterate_gemv_stream<8>;
+        default: return nullptr;
+    }
+}
+
+int stream_rows_per_block(int cpl) {
+    switch (cpl) {
+        case 1: return StreamShape<1>::ROWS;
+        case 2: return StreamShape<2>::ROWS;
+        case 4: return StreamShape<4>::ROWS;
+        case 8: return StreamShape<8>::ROWS;
+        default: return 0;
+    }
+}
+
 // ------------------------------------------------------------ GRAM path
 // Shared memory: r (Rpad) | w2 (Rpad) | x slice (spad) | x* slice (spad) |
 // full x for the refresh (npad)
@@ -776,6 +1022,26 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
         }
     }
     if (variant == 2 && cfg->reg_rpw == 0) return CSK_EUNSUPPORTED;
+    // rows streamed through a bulk-copy ring: on request, or when the rows
+    // stay resident neither in registers nor in shared memory
+    cfg->stream_cpl = 0;
+    if (path == CSK_RESID_GEMV && dtype == CSK_F32 && vec_ok && n % 4 == 0 &&
+        (variant == 3 || (variant == 0 && cfg->reg_rpw == 0 && !cfg->cache_rows))) {
+        const int need_c = (n / 4 + 31) / 32;
+        const int cpl = need_c <= 1 ? 1 : need_c <= 2 ? 2 : need_c <= 4 ? 4 : need_c <= 8 ? 8 : 0;
+        int nst = kMaxStreamStages;
+        while (cpl && nst > 2 && stream_smem_bytes(R, n, stream_rows_per_block(cpl), nst) > budget)
+            --nst;
+        const size_t sm = cpl ? stream_smem_bytes(R, n, stream_rows_per_block(cpl), nst) : 0;
+        if (cpl && sm <= budget) {
+            cfg->stream_cpl = cpl;
+            cfg->stream_stages = nst;
+            cfg->reg_rpw = cfg->reg_cpl = 0;
+            cfg->cache_rows = 0;
+            cfg->smem = sm;
+        }
+    }
+    if (variant == 3 && cfg->stream_cpl == 0) return CSK_EUNSUPPORTED;
     if (cfg->smem > budget) return CSK_EUNSUPPORTED;
     return CSK_OK;
 }
@@ -783,7 +1049,9 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
 cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st) {
     void* fn;
     const bool reg = cfg.reg_rpw > 0;
+    const bool stream = cfg.stream_cpl > 0;
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
+    else if (stream) fn = const_cast<void*>(stream_kernel(cfg.stream_cpl));
     else if (reg) fn = const_cast<void*>(reg_kernel(cfg.reg_rpw, cfg.reg_cpl));
     else if (p.dtype == CSK_F64) fn = (void*)k_iterate_gemv<double>;
     else fn = (void*)k_iterate_gemv<float>;
@@ -797,11 +1065,13 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     dev_info(&di);
     if ((int64_t)per_sm * di.sms < cfg.grid) return cudaErrorCooperativeLaunchTooLarge;
     IterProblem pc = p;
-    int R = cfg.rows_per_cta, cache = cfg.cache_rows;
+    int R = cfg.rows_per_cta, cache = cfg.cache_rows, nst = cfg.stream_stages;
     void* args_gemv[] = {&pc, &R, &cache};
     void* args_gram[] = {&pc, &R};
+    void* args_stream[] = {&pc, &R, &nst};
     e = cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(cfg.threads),
-                                    (path == CSK_RESID_GRAM || reg) ? args_gram : args_gemv,
+                                    stream ? args_stream
+                                           : (path == CSK_RESID_GRAM || reg) ? args_gram : args_gemv,
                                     cfg.smem, st);
     if (e == cudaSuccess) note_launches(1);
     return e;

@@ -70,6 +70,8 @@ struct IterConfig {
     int cache_rows = 0;     // At slice resident in shared memory (GEMV path)
     int reg_rpw = 0;        // >0: register-resident GEMV variant, rows per warp
     int reg_cpl = 0;        //     and float4 columns per lane
+    int stream_cpl = 0;     // >0: rows streamed through a bulk-copy ring (FP32 GEMV)
+    int stream_stages = 0;  //     and the ring's depth in blocks
     size_t smem = 0;        // dynamic shared memory bytes
 };
 

@@ -266,3 +266,57 @@ def test_bench_launch_configuration_matches_oracle(csk):
     _compare_prefix(ik, ref, 1e-3)
     _check_steps(At32, bt32, X, ik, info["iters"] - 1, 2.0 ** -24)
     assert abs(info["iters"] - ref.iters) <= 0.05 * ref.iters
+
+
+@pytest.mark.parametrize("grid", [60, 79, 128])
+def test_stream_variant_equals_register_variant(csk, grid):
+    """Rows streamed through the bulk-copy ring (variant 3) use the register
+    variant's arithmetic in the same order: identical iterates, bit for bit."""
+    m, n, d, seed = 40000, 200, 2000, 12
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x2, i2, k2 = _solve(csk, s, d, seed, log=3000, grid=grid, gemv_variant=2)
+    x3, i3, k3 = _solve(csk, s, d, seed, log=3000, grid=grid, gemv_variant=3)
+    assert i2["status"] == 0 and i3["status"] == 0 and i3["rse"] <= 1e-6
+    assert i2["iters"] == i3["iters"] and np.array_equal(k2, k3)
+    assert np.array_equal(x2.view(np.uint32), x3.view(np.uint32))
+
+
+@pytest.mark.parametrize("pad", [0, 4])
+def test_stream_variant_unsketched_mwrk(csk, pad):
+    """MWRK on A itself (Remark 1, d = 0) streams A every step: the oracle's
+    row sequence up to the first near-tie, valid steps, RES <= 1e-6, for a
+    packed A (one bulk copy per block) and a strided one (one per row)."""
+    m, n, seed = 30000, 120, 13
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    Ad = torch.zeros((m, n + pad), dtype=torch.float32, device=DEV)
+    Ad[:, :n] = _to(s.A)
+    A = Ad[:, :n]
+    ik = torch.full((20000,), -1, dtype=torch.int32, device=DEV)
+    X = torch.zeros((20000, n), dtype=torch.float32, device=DEV)
+    p = csk.csk_params_default(d=0, path=csk.GEMV, gemv_variant=3, ik_log=ik.data_ptr(),
+                               ik_log_len=20000, x_log=X.data_ptr(), x_log_len=20000)
+    x, info = csk.csk_solve(A, _to(s.b), p, x_star=_to(s.x_star.astype(np.float32)))
+    ref = oracle.mwrk(s.A.astype(np.float64), s.b.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+    ikh = ik.cpu().numpy()[:info["iters"]]
+    _compare_prefix(ikh, ref, 1e-3)
+    _check_steps(s.A, s.b, X.cpu().numpy(), ikh, min(info["iters"] - 1, 200), 2.0 ** -24)
+    assert abs(info["iters"] - ref.iters) <= max(3, 0.05 * ref.iters)
+
+
+def test_stream_variant_idle_ctas_and_timeout(csk):
+    """More CTAs than rows (CTAs with an empty row range stream nothing), and
+    the bounded waits: CTA 0 never publishes -> CSK_ETIMEOUT, context
+    survives."""
+    s = synth.gaussian_system(3000, 40, 14, np.float32)
+    x, info, _ = _solve(csk, s, 120, 14, grid=128, gemv_variant=3)     # CTAs 120..127 idle
+    ref = oracle.csk(s.A.astype(np.float64), s.b.astype(np.float64), 120, 14, x_star=s.x_star)
+    assert info["status"] == ref.status
+    if ref.status == 0:
+        assert info["rse"] <= 1e-6 and abs(info["iters"] - ref.iters) <= max(3, 0.05 * ref.iters)
+    x, info, _ = _solve(csk, s, 400, 14, grid=16, gemv_variant=3, spin_limit=20000,
+                        fault_inject=1)
+    assert info["status"] == -3
+    x, info, _ = _solve(csk, s, 400, 14, grid=16, gemv_variant=3)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
