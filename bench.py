@@ -46,6 +46,10 @@ def sketch_bytes(m, n, d, s=4):
     return s * m * n + s * m + 8 * m + s * d * n + s * d + 8 * d
 
 
+LOOP_KERNELS = {1: "k_iterate_gemv", 2: "k_iterate_gemv_reg", 3: "k_iterate_gemv_stream"}
+LOOP_VARIANTS = {0: "auto", 1: "shared-memory rows", 2: "register rows", 3: "streamed rows (TMA ring)"}
+
+
 def gemv_bytes_per_eval(d, n, s=4):
     # At (d x n) once per residual evaluation, plus bt, x and the row update
     return s * d * n + s * (d + 2 * n)
@@ -201,7 +205,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=0, help="loop CTA count (0 = autotune)")
-    ap.add_argument("--variant", type=int, default=0, help="loop variant 1/2 (0 = autotune)")
+    ap.add_argument("--variant", type=int, default=0, help="loop variant 1-3 (0 = autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -293,17 +297,21 @@ def main():
     pm = csk.csk_params_default(d=0, tol=TOL, path=csk.GEMV)
     wsm = csk._workspace(csk.csk_solve_workspace_size(M, N_COLS, csk.CSK_F32, pm), dev)
     csk.csk_solve(A, b, pm, x_star=xs, ws=wsm)
-    m0 = torch.cuda.Event(enable_timing=True)
-    m1 = torch.cuda.Event(enable_timing=True)
-    RM = 2
-    m0.record()
-    for _ in range(RM):
-        _, inf_m = csk.csk_solve(A, b, pm, x_star=xs, ws=wsm, sync=False)
-    m1.record()
+    RM = 3
+    mev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(RM)]
+    mrec = []
+    for i in range(RM):
+        csk.set_stage_events(pm, mev[i])
+        _, inf_m = csk.csk_solve(A, b, pm, x_star=xs, ws=wsm)
+        mrec.append(inf_m)
     torch.cuda.synchronize()
-    inf_m = csk.read_info(inf_m)
-    mwrk = {"ms": m0.elapsed_time(m1) / RM, "iters": inf_m["iters"], "rse": inf_m["rse"],
-            "status": inf_m["status"]}
+    m_tot = float(np.median([e[0].elapsed_time(e[4]) for e in mev]))
+    m_loop = float(np.median([e[2].elapsed_time(e[3]) for e in mev]))
+    m_it = mrec[0]["iters"]
+    # the loop streams A once per residual evaluation (IT + 1 of them)
+    m_gbs = (m_it + 1) * gemv_bytes_per_eval(M, N_COLS) / (m_loop * 1e-3) / 1e9
+    mwrk = {"ms": m_tot, "loop_ms": m_loop, "iters": m_it, "rse": mrec[0]["rse"],
+            "status": mrec[0]["status"], "stream_gbs": m_gbs}
     del wsm
 
     from paper_2004_02480_gb300 import replicas
@@ -324,8 +332,8 @@ def main():
     sk_ms = float(np.mean(st_sketch))
     sk_gbs = sketch_bytes(M, N_COLS, D) / (sk_ms * 1e-3) / 1e9
     src = _source_hash("paper_2004_02480_gb300/csrc/iterate.cu", "paper_2004_02480_gb300/csrc/common.cuh")
-    traffic = _traffic(("k_iterate_gemv_reg" if tuned["gemv_variant"] == 2 else "k_iterate_gemv")
-                       + "_100000x500_d5000", src)
+    loop_kernel = LOOP_KERNELS.get(tuned["gemv_variant"], "k_iterate_gemv")
+    traffic = _traffic(loop_kernel + "_100000x500_d5000", src)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -342,8 +350,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded N(0,1), paper Section 3 recipe)",
         "config": {"workload": WORKLOAD, "m": M, "n": N_COLS, "d": D, "tol": TOL, "path": "gemv",
                    "parallelism": f"replicas x{world} (independent systems)",
-                   "loop": {"grid": tuned["grid"], "variant": ["auto", "shared-memory rows",
-                                                               "register rows"][tuned["gemv_variant"]],
+                   "loop": {"grid": tuned["grid"], "variant": LOOP_VARIANTS.get(tuned["gemv_variant"]),
                             "autotuned_us_per_step": tuned["us_per_step"]},
                    "l2": "inputs larger than L2 (A = 200 MB > 129 MB)"},
         "valid": bool(ok),
@@ -351,7 +358,7 @@ def main():
                       "iters_mean": mean_it, "rse_max": max(r["rse"] for r in recs),
                       "grid": recs[0]["grid"],
                       "sketch_gbs": sk_gbs, "sketch_frac_of_" + peak_kind + "_hbm": sk_gbs / hbm},
-        "roofline": {"kernel": ("k_iterate_gemv_reg" if tuned["gemv_variant"] == 2 else "k_iterate_gemv<float>"),
+        "roofline": {"kernel": loop_kernel,
                      "bound": "hbm", "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
                      "traffic": traffic,
@@ -363,10 +370,15 @@ def main():
                 "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok),
                 "call": f"csk_solve_host_many over {E} solves from page-locked host memory "
                         "(the copies of solve k+1 overlap solve k)"},
-        "comparison": {"mwrk_unsketched_ms": mwrk["ms"], "mwrk_iters": mwrk["iters"],
-                       "mwrk_rse": mwrk["rse"], "mwrk_status": mwrk["status"],
+        "comparison": {"mwrk_unsketched_ms": mwrk["ms"], "mwrk_loop_ms": mwrk["loop_ms"],
+                       "mwrk_iters": mwrk["iters"], "mwrk_rse": mwrk["rse"],
+                       "mwrk_status": mwrk["status"],
+                       "mwrk_loop_kernel": "k_iterate_gemv_stream (A streamed from HBM every step)",
+                       "mwrk_loop_gbs": mwrk["stream_gbs"],
+                       "mwrk_loop_frac_of_" + peak_kind + "_hbm": mwrk["stream_gbs"] / hbm,
                        "csk_ms": ms / K, "csk_speedup_over_mwrk": mwrk["ms"] / (ms / K),
-                       "note": "MWRK (d = 0) on the same A, b on the GPU, 2 runs; not part of the timed steps"},
+                       "note": "MWRK (d = 0, Remark 1) on the same A, b on the GPU, median of 3 "
+                               "solves; not part of the timed steps"},
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
