@@ -113,6 +113,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
     t = (a - (s - bb)) + (b - bb);
 }
 
+constexpr int kGChunk = 16;    // G-row values per thread in flight at once
+constexpr int kXChunk = 4;     // At-row values per thread in flight at once
+
 __device__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
                            int64_t max_iter, int refresh) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
@@ -164,33 +167,61 @@ __device__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& s
             }
             __syncthreads();
         }
-        // one pass: apply the previous step's update, then score
+        // one pass: apply the previous step's update, then score.  Each
+        // thread walks rows tid, tid + nt, ... as before, but issues the
+        // loads of a whole chunk of G[idx, :] (and of its part of At[idx, :])
+        // before using any, so a step waits for one memory round trip, not
+        // one per row.
         Red<float> c;
         c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
         const float* grow = idx >= 0 ? S.G + (int64_t)idx * S.ldg : nullptr;
-        for (int j = tid; j < d; j += nt) {
-            float r = rs[j];
-            if (grow) {
-                r = (j == idx) ? 0.0f : fmaf(-alpha, __ldg(grow + j), r);
-                rs[j] = r;
-            }
-            const float w = w2s[j];
-            if (!(w < 0.0f)) {
-                const float key = r * r * w;
-                if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = j; }
-            }
-            if (!S.Xstar) c.stat += r * r;
-        }
         const float* arow = idx >= 0 ? S.At + (int64_t)idx * n : nullptr;
-        for (int col = tid; col < n; col += nt) {
-            float x = xs[col];
-            if (arow) {
-                x = fmaf(alpha, __ldg(arow + col), x);
-                xs[col] = x;
+        float av[kXChunk];
+#pragma unroll
+        for (int q = 0; q < kXChunk; ++q) {
+            const int col = tid + q * nt;
+            av[q] = (arow && col < n) ? __ldg(arow + col) : 0.0f;
+        }
+        for (int base = 0; base < d; base += kGChunk * nt) {
+            float gv[kGChunk];
+#pragma unroll
+            for (int q = 0; q < kGChunk; ++q) {
+                const int j = base + q * nt + tid;
+                gv[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
             }
-            if (S.Xstar) {
-                const float t = x - xss[col];
-                c.stat += t * t;
+#pragma unroll
+            for (int q = 0; q < kGChunk; ++q) {
+                const int j = base + q * nt + tid;
+                if (j < d) {
+                    float r = rs[j];
+                    if (grow) {
+                        r = (j == idx) ? 0.0f : fmaf(-alpha, gv[q], r);
+                        rs[j] = r;
+                    }
+                    const float w = w2s[j];
+                    if (!(w < 0.0f)) {
+                        const float key = r * r * w;
+                        if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = j; }
+                    }
+                    if (!S.Xstar) c.stat += r * r;
+                }
+            }
+        }
+        for (int base = 0; base < n; base += kXChunk * nt) {
+#pragma unroll
+            for (int q = 0; q < kXChunk; ++q) {
+                const int col = base + q * nt + tid;
+                if (col < n) {
+                    float x = xs[col];
+                    if (arow) {
+                        x = fmaf(alpha, base == 0 ? av[q] : __ldg(arow + col), x);
+                        xs[col] = x;
+                    }
+                    if (S.Xstar) {
+                        const float t = x - xss[col];
+                        c.stat += t * t;
+                    }
+                }
             }
         }
         c = block_reduce(c, sh, par);
