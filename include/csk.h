@@ -90,9 +90,10 @@ typedef struct {
                                they do not fit), 2 = rows of At in registers
                                (FP32, n <= 512, n % 4 == 0, few rows per CTA),
                                3 = rows streamed every step through a shared-
-                               memory ring of bulk copies (FP32, n <= 1024,
-                               n % 4 == 0; the choice when rows fit neither
-                               registers nor shared memory)                     */
+                               memory ring of bulk copies (n a multiple of 16
+                               bytes, n <= 1024 FP32 / 512 FP64; the choice
+                               when rows fit neither registers nor shared
+                               memory)                                          */
     void *stage_events[5];  /* optional cudaEvent_t handles (caller-owned), each
                                recorded on the stream when non-NULL: [0] before
                                the sketch, [1] after sketch and row norms, [2]

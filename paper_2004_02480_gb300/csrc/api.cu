@@ -148,7 +148,8 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     const int rows = (int)(d > 0 ? d : m);
     IterConfig cfg;
     const int64_t ld_it = d > 0 ? n : lda;
-    const bool vec_ok = (ld_it % 4 == 0) &&
+    const int vlen = dtype == CSK_F64 ? 2 : 4;   // elements per 16-byte chunk
+    const bool vec_ok = (ld_it % vlen == 0) &&
                         (d > 0 || reinterpret_cast<uintptr_t>(A) % 16 == 0);
     int rc = plan_iterate(path, dtype, rows, (int)n, params->grid, params->gemv_variant, vec_ok,
                           &cfg);

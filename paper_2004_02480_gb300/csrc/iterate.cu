@@ -249,6 +249,19 @@ __device__ __forceinline__ T weight_of(double N) {
     return N > 0.0 ? (T)(1.0 / N) : (N == 0.0 ? T(-1) : (T)NAN);
 }
 
+// Sum of squares of a 16-byte chunk of x - x*, rounded in a fixed order (no
+// contraction left to the compiler), so the register and streamed loops
+// compute the stopping statistic identically.
+__device__ __forceinline__ float chunk_sq(const float (&t)[4]) {
+    float s = __fmul_rn(t[0], t[0]);
+    s = __fmaf_rn(t[1], t[1], s);
+    s = __fmaf_rn(t[2], t[2], s);
+    return __fmaf_rn(t[3], t[3], s);
+}
+__device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
+    return __fma_rn(t[1], t[1], __dmul_rn(t[0], t[0]));
+}
+
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
 template <typename T>
@@ -468,9 +481,9 @@ k_iterate_gemv_reg(IterProblem p, int R) {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
                 if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
-                    const float ex = xr[i].x - xsr[i].x, ey = xr[i].y - xsr[i].y;
-                    const float ez = xr[i].z - xsr[i].z, ew = xr[i].w - xsr[i].w;
-                    c.stat += ex * ex + ey * ey + ez * ez + ew * ew;
+                    const float t[4] = {xr[i].x - xsr[i].x, xr[i].y - xsr[i].y,
+                                        xr[i].z - xsr[i].z, xr[i].w - xsr[i].w};
+                    c.stat += chunk_sq(t);
                 }
             }
         }
@@ -565,44 +578,64 @@ bool reg_shape(int rows_per_cta, int n, int* rpw, int* cpl) {
 constexpr int kMaxStreamStages = CSK_STREAM_MAX_STAGES;   // ring depth: as many as fit, up to this
 constexpr uint32_t kStreamWait = 1u << 24;      // try_wait polls per bulk-copy wait
 
-template <int CPL>
-struct StreamShape {
-    static constexpr int RPB = CPL <= 2 ? 4 : 8 / CPL;   // rows per warp per block
-    static constexpr int ROWS = kWarps * RPB;            // rows per block (<= 32 KB)
+// A 16-byte chunk of a row: four floats or two doubles.
+template <typename T> struct Chunk;
+template <> struct Chunk<float> {
+    static constexpr int V = 4;
+    using vec = float4;
+    __device__ static void get(const vec& v, float (&e)[4]) { e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w; }
+    __device__ static vec put(const float (&e)[4]) { return make_float4(e[0], e[1], e[2], e[3]); }
+};
+template <> struct Chunk<double> {
+    static constexpr int V = 2;
+    using vec = double2;
+    __device__ static void get(const vec& v, double (&e)[2]) { e[0] = v.x; e[1] = v.y; }
+    __device__ static vec put(const double (&e)[2]) { return make_double2(e[0], e[1]); }
 };
 
-size_t stream_smem_bytes(int R, int n, int rows_per_blk, int stages) {
-    return (size_t)stages * rows_per_blk * n * 4 + (size_t)2 * ((R + 3) & ~3) * 4;
+// Rows per warp per block: a block holds kWarps * RPB rows of at most
+// 32 * CPL chunks (<= 32 KB).
+template <int CPL>
+struct StreamShape {
+    static constexpr int RPB = CPL <= 2 ? 4 : 8 / CPL;
+    static constexpr int ROWS = kWarps * RPB;
+};
+
+size_t stream_smem_bytes(int R, int n, int esize, int rows_per_blk, int stages) {
+    return (size_t)stages * rows_per_blk * n * esize + (size_t)2 * ((R + 3) & ~3) * esize;
 }
 
-template <int CPL>
+template <typename T, int CPL>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     constexpr int RPB = StreamShape<CPL>::RPB, SR = StreamShape<CPL>::ROWS;
+    constexpr int V = Chunk<T>::V;
+    using vec = typename Chunk<T>::vec;
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ RedShared<float> sh;
+    __shared__ RedShared<T> sh;
     __shared__ __align__(8) uint64_t full[kMaxStreamStages];
     __shared__ __align__(8) uint64_t empty[kMaxStreamStages];
     int par = 0;
     const int b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int n = p.n, d = p.d, n4 = n >> 2;
+    const int n = p.n, d = p.d, nv = n / V;          // 16-byte chunks per row
     const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
     const int nblk = (nr + SR - 1) / SR;
-    const size_t blk_floats = (size_t)SR * n;
-    float* ring = reinterpret_cast<float*>(dsm);
-    float* bts = ring + nst * blk_floats;
-    float* w2s = bts + ((R + 3) & ~3);
-    const float* At = static_cast<const float*>(p.At);
-    const float* bt = static_cast<const float*>(p.bt);
-    const float* x0 = static_cast<const float*>(p.x0);
-    const float* xstar = static_cast<const float*>(p.xstar);
+    const size_t blk_elems = (size_t)SR * n;
+    const uint32_t row_bytes = (uint32_t)n * sizeof(T);
+    T* ring = reinterpret_cast<T*>(dsm);
+    T* bts = ring + nst * blk_elems;
+    T* w2s = bts + ((R + 3) & ~3);
+    const T* At = static_cast<const T*>(p.At);
+    const T* bt = static_cast<const T*>(p.bt);
+    const T* x0 = static_cast<const T*>(p.x0);
+    const T* xstar = static_cast<const T*>(p.xstar);
     const bool stat_owner = (b == 0 && warp == 0);
     const bool packed = p.ld == n;
 
     for (int q = tid; q < nr; q += blockDim.x) {
         bts[q] = bt[r0 + q];
-        w2s[q] = weight_of<float>(p.N2[r0 + q]);
+        w2s[q] = weight_of<T>(p.N2[r0 + q]);
     }
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -626,14 +659,14 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 return false;
             const int q0 = iblk * SR, rows = min(SR, nr - q0);
             const uint32_t bar = smem_u32(&full[is]);
-            const uint32_t dst = smem_u32(ring + is * blk_floats);
-            mbar_expect_tx(bar, (uint32_t)rows * n * 4);
+            const uint32_t dst = smem_u32(ring + is * blk_elems);
+            mbar_expect_tx(bar, (uint32_t)rows * row_bytes);
             if (packed) {
-                bulk_g2s(dst, At + (int64_t)(r0 + q0) * n, (uint32_t)rows * n * 4, bar);
+                bulk_g2s(dst, At + (int64_t)(r0 + q0) * n, (uint32_t)rows * row_bytes, bar);
             } else {
                 for (int q = 0; q < rows; ++q)
-                    bulk_g2s(dst + (uint32_t)q * n * 4, At + (int64_t)(r0 + q0 + q) * p.ld,
-                             (uint32_t)n * 4, bar);
+                    bulk_g2s(dst + (uint32_t)q * row_bytes, At + (int64_t)(r0 + q0 + q) * p.ld,
+                             row_bytes, bar);
             }
             if (++iblk == nblk) iblk = 0;
             if (++is == nst) { is = 0; ilap ^= 1u; }
@@ -643,15 +676,16 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     int stalled = 0;
     if (tid == 0 && nblk > 0 && !refill(nst)) stalled = 1;
 
-    float4 xr[CPL], xsr[CPL];
+    T xr[CPL][V], xsr[CPL][V];
 #pragma unroll
     for (int i = 0; i < CPL; ++i) {
-        const int c4 = lane + 32 * i;
-        xr[i] = (x0 && c4 < n4) ? reinterpret_cast<const float4*>(x0)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        xsr[i] = (xstar && c4 < n4) ? reinterpret_cast<const float4*>(xstar)[c4]
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int c = lane + 32 * i;
+#pragma unroll
+        for (int e = 0; e < V; ++e) { xr[i][e] = T(0); xsr[i][e] = T(0); }
+        if (x0 && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(x0)[c], xr[i]);
+        if (xstar && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(xstar)[c], xsr[i]);
     }
-    const float threshold = (float)(p.tol * *p.stop_norm);
+    const T threshold = (T)(p.tol * *p.stop_norm);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     uint32_t round = 0;
     int64_t k = 0, g = 0;          // g: blocks consumed (the same count in every warp)
@@ -659,8 +693,8 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     uint32_t clap = 0;
     int status = CSK_OK;
     for (;;) {
-        Red<float> c;
-        c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
+        Red<T> c;
+        c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
         for (int blk = 0; blk < nblk && !stalled; ++blk, ++g) {
             const int s = cs;
             const uint32_t lap = clap;
@@ -669,38 +703,40 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 stalled = 1;
                 break;
             }
-            const float* rows = ring + s * blk_floats;
+            const T* rows = ring + s * blk_elems;
             const int q0 = blk * SR;
-            float dot[RPB];
+            T dot[RPB];
 #pragma unroll
             for (int u = 0; u < RPB; ++u) {
-                const float4* row = reinterpret_cast<const float4*>(rows + (size_t)(warp + kWarps * u) * n);
+                const vec* row = reinterpret_cast<const vec*>(rows + (size_t)(warp + kWarps * u) * n);
                 const bool live = q0 + warp + kWarps * u < nr;
-                float acc = 0.0f;
+                T acc = T(0);
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
-                    const int c4 = lane + 32 * i;
-                    if (live && c4 < n4) {
-                        const float4 a = row[c4];
-                        acc = fmaf(a.x, xr[i].x, acc);
-                        acc = fmaf(a.y, xr[i].y, acc);
-                        acc = fmaf(a.z, xr[i].z, acc);
-                        acc = fmaf(a.w, xr[i].w, acc);
+                    const int cc = lane + 32 * i;
+                    if (live && cc < nv) {
+                        T a[V];
+                        Chunk<T>::get(row[cc], a);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) acc = fma(a[e], xr[i][e], acc);
                     }
                 }
                 dot[u] = acc;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
-            warp_sum_rows<RPB>(dot);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < RPB; ++u) dot[u] += __shfl_xor_sync(0xffffffffu, dot[u], o);
 #pragma unroll
             for (int u = 0; u < RPB; ++u) {
                 const int q = q0 + warp + kWarps * u;
                 if (q < nr) {
-                    const float r = bts[q] - dot[u];
-                    const float w = w2s[q];
-                    if (!(w < 0.0f)) {
-                        const float key = r * r * w;
+                    const T r = bts[q] - dot[u];
+                    const T w = w2s[q];
+                    if (!(w < T(0))) {
+                        const T key = r * r * w;
                         if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
                     }
                     if (!xstar && lane == 0) c.stat += r * r;
@@ -719,10 +755,11 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
         if (xstar && warp == 0) {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
-                    const float ex = xr[i].x - xsr[i].x, ey = xr[i].y - xsr[i].y;
-                    const float ez = xr[i].z - xsr[i].z, ew = xr[i].w - xsr[i].w;
-                    c.stat += ex * ex + ey * ey + ez * ez + ew * ew;
+                if (lane + 32 * i < nv && (lane + 32 * i) % (int)gridDim.x == b) {
+                    T t[V];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) t[e] = xr[i][e] - xsr[i][e];
+                    c.stat += chunk_sq(t);
                 }
             }
         }
@@ -738,18 +775,18 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
         if (stat_owner && p.x_log && k < p.x_log_len)
 #pragma unroll
             for (int i = 0; i < CPL; ++i)
-                if (lane + 32 * i < n4)
-                    reinterpret_cast<float4*>(static_cast<float*>(p.x_log) + k * n)[lane + 32 * i] = xr[i];
-        const float4* arow = reinterpret_cast<const float4*>(At + (int64_t)c.idx * p.ld);
+                if (lane + 32 * i < nv)
+                    reinterpret_cast<vec*>(static_cast<T*>(p.x_log) + k * n)[lane + 32 * i] =
+                        Chunk<T>::put(xr[i]);
+        const vec* arow = reinterpret_cast<const vec*>(At + (int64_t)c.idx * p.ld);
 #pragma unroll
         for (int i = 0; i < CPL; ++i) {
-            const int c4 = lane + 32 * i;
-            if (c4 < n4) {
-                const float4 v = __ldg(arow + c4);
-                xr[i].x = fmaf(c.alpha, v.x, xr[i].x);
-                xr[i].y = fmaf(c.alpha, v.y, xr[i].y);
-                xr[i].z = fmaf(c.alpha, v.z, xr[i].z);
-                xr[i].w = fmaf(c.alpha, v.w, xr[i].w);
+            const int cc = lane + 32 * i;
+            if (cc < nv) {
+                T v[V];
+                Chunk<T>::get(__ldg(arow + cc), v);
+#pragma unroll
+                for (int e = 0; e < V; ++e) xr[i][e] = fma(c.alpha, v[e], xr[i][e]);
             }
         }
         ++k;
@@ -761,20 +798,21 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
             if (++cs == nst) { cs = 0; clap ^= 1u; }
         }
     if (stat_owner) {
-        float4* xo = reinterpret_cast<float4*>(p.x_out);
+        vec* xo = reinterpret_cast<vec*>(p.x_out);
 #pragma unroll
         for (int i = 0; i < CPL; ++i)
-            if (lane + 32 * i < n4) xo[lane + 32 * i] = xr[i];
+            if (lane + 32 * i < nv) xo[lane + 32 * i] = Chunk<T>::put(xr[i]);
     }
     finish(p.info, status, k);
 }
 
-const void* stream_kernel(int cpl) {
+const void* stream_kernel(int dtype, int cpl) {
+    const bool f64 = dtype == CSK_F64;
     switch (cpl) {
-        case 1: return (const void*)k_iterate_gemv_stream<1>;
-        case 2: return (const void*)k_iterate_gemv_stream<2>;
-        case 4: return (const void*)k_iterate_gemv_stream<4>;
-        case 8: return (const void*)k_iterate_gemv_stream<8>;
+        case 1: return f64 ? (const void*)k_iterate_gemv_stream<double, 1> : (const void*)k_iterate_gemv_stream<float, 1>;
+        case 2: return f64 ? (const void*)k_iterate_gemv_stream<double, 2> : (const void*)k_iterate_gemv_stream<float, 2>;
+        case 4: return f64 ? (const void*)k_iterate_gemv_stream<double, 4> : (const void*)k_iterate_gemv_stream<float, 4>;
+        case 8: return f64 ? (const void*)k_iterate_gemv_stream<double, 8> : (const void*)k_iterate_gemv_stream<float, 8>;
         default: return nullptr;
     }
 }
@@ -991,9 +1029,12 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
     if (G > d) G = d;
     if (G < 1) G = 1;
     if (grid_req <= 0) {
-        // small problems: fewer CTAs, cheaper exchange
+        // small problems: fewer CTAs, cheaper exchange -- about 16K cells of
+        // At per CTA in FP32, 1K in FP64 (this GPU's FP64 rate is 1/64 of
+        // its FP32 rate, so a step's dot products need more SMs)
         const int64_t cells = (int64_t)d * n;
-        int64_t want = (cells + 16383) / 16384;          // ~16K cells of At per CTA
+        const int64_t per_cta = dtype == CSK_F64 ? 1024 : 16384;
+        int64_t want = (cells + per_cta - 1) / per_cta;
         if (want < 1) want = 1;
         if (want < G) G = (int)want;
     }
@@ -1025,14 +1066,15 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
     // rows streamed through a bulk-copy ring: on request, or when the rows
     // stay resident neither in registers nor in shared memory
     cfg->stream_cpl = 0;
-    if (path == CSK_RESID_GEMV && dtype == CSK_F32 && vec_ok && n % 4 == 0 &&
+    const int vlen = 16 / s;                 // elements per 16-byte chunk
+    if (path == CSK_RESID_GEMV && vec_ok && n % vlen == 0 &&
         (variant == 3 || (variant == 0 && cfg->reg_rpw == 0 && !cfg->cache_rows))) {
-        const int need_c = (n / 4 + 31) / 32;
+        const int need_c = (n / vlen + 31) / 32;
         const int cpl = need_c <= 1 ? 1 : need_c <= 2 ? 2 : need_c <= 4 ? 4 : need_c <= 8 ? 8 : 0;
         int nst = kMaxStreamStages;
-        while (cpl && nst > 2 && stream_smem_bytes(R, n, stream_rows_per_block(cpl), nst) > budget)
+        while (cpl && nst > 2 && stream_smem_bytes(R, n, s, stream_rows_per_block(cpl), nst) > budget)
             --nst;
-        const size_t sm = cpl ? stream_smem_bytes(R, n, stream_rows_per_block(cpl), nst) : 0;
+        const size_t sm = cpl ? stream_smem_bytes(R, n, s, stream_rows_per_block(cpl), nst) : 0;
         if (cpl && sm <= budget) {
             cfg->stream_cpl = cpl;
             cfg->stream_stages = nst;
@@ -1051,7 +1093,7 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     const bool reg = cfg.reg_rpw > 0;
     const bool stream = cfg.stream_cpl > 0;
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
-    else if (stream) fn = const_cast<void*>(stream_kernel(cfg.stream_cpl));
+    else if (stream) fn = const_cast<void*>(stream_kernel(p.dtype, cfg.stream_cpl));
     else if (reg) fn = const_cast<void*>(reg_kernel(cfg.reg_rpw, cfg.reg_cpl));
     else if (p.dtype == CSK_F64) fn = (void*)k_iterate_gemv<double>;
     else fn = (void*)k_iterate_gemv<float>;

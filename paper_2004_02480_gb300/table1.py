@@ -1,0 +1,113 @@
+"""Table 1 of the paper on one GPU: CSK against MWRK on A itself.
+
+Shapes m in {3..7} x 10^5, n in {50, 100, 150}, d = n^2; A and x* iid N(0,1),
+b = A x*, x0 = 0, stop at RES <= 1e-6 or 20000 steps (Section 3).  The paper
+averages 50 trials; each trial here is a seeded Gaussian draw generated on the
+device (not timed) in binary64, as the paper's MATLAB runs presumably are.
+Both methods run through csk_solve: CSK with the count sketch of seed
+`trial`, MWRK with d = 0 (Remark 1).  Times are CUDA-event times of the whole
+call (sketch, iteration and the final check), and IT the step count.
+
+The paper's own means (Table 1: MATLAB on an unstated CPU) are printed beside
+ours as context.
+
+    python -m paper_2004_02480_gb300.table1 --trials 50
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+# Table 1: (m, n) -> (CSK IT, MWRK IT, CSK s, MWRK s, speedup), means of 50 trials
+PAPER = {
+    (300000, 50): (54.90, 31, 0.2209, 1.6878, 7.6393),
+    (300000, 100): (94.86, 63, 0.4569, 5.1097, 11.1840),
+    (300000, 150): (132.76, 96, 1.4894, 10.3728, 6.9645),
+    (400000, 50): (54.36, 29, 0.2597, 1.9737, 7.6005),
+    (400000, 100): (95.14, 60, 0.5778, 6.0903, 10.5403),
+    (400000, 150): (132.56, 94, 1.8509, 13.1016, 7.0783),
+    (500000, 50): (55.10, 29, 0.3312, 2.5878, 7.8123),
+    (500000, 100): (94.96, 60, 0.7366, 8.2903, 11.2554),
+    (500000, 150): (132.54, 91, 2.0513, 17.3091, 8.4383),
+    (600000, 50): (54.88, 28, 0.4053, 3.1672, 7.8142),
+    (600000, 100): (95.16, 58, 0.8566, 10.2019, 11.9103),
+    (600000, 150): (132.58, 92, 2.3828, 22.0388, 9.2490),
+    (700000, 50): (54.70, 29, 0.4550, 3.9312, 8.6401),
+    (700000, 100): (95.42, 58, 1.0025, 12.2144, 12.1839),
+    (700000, 150): (132.36, 89, 2.7194, 25.7228, 9.4591),
+}
+
+
+def run_shape(csk, torch, m: int, n: int, trials: int, dev) -> dict:
+    d = n * n
+    pc = csk.csk_params_default(d=d, tol=1e-6, max_iter=20000)
+    pm = csk.csk_params_default(d=0, tol=1e-6, max_iter=20000)
+    ws = csk._workspace(max(csk.csk_solve_workspace_size(m, n, csk.CSK_F64, pc),
+                            csk.csk_solve_workspace_size(m, n, csk.CSK_F64, pm)), dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    info = torch.zeros(64, dtype=torch.uint8, device=dev)
+    gen = torch.Generator(device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    it_c, it_m, t_c, t_m, ok = [], [], [], [], True
+    for trial in range(trials):
+        gen.manual_seed(1_000_003 * trial + 7919 * m + n)
+        A = torch.randn((m, n), generator=gen, dtype=torch.float64, device=dev)
+        xs = torch.randn(n, generator=gen, dtype=torch.float64, device=dev)
+        b = A @ xs
+        pc.seed = trial
+        ev[0].record()
+        csk.csk_solve(A, b, pc, x_star=xs, x_out=x, info=info, ws=ws, sync=False)
+        ev[1].record()
+        rc = csk.read_info(info)
+        it_c.append(rc["iters"])
+        ok &= rc["status"] == 0 and rc["rse"] <= 1e-6
+        ev[2].record()
+        csk.csk_solve(A, b, pm, x_star=xs, x_out=x, info=info, ws=ws, sync=False)
+        ev[3].record()
+        rm = csk.read_info(info)
+        it_m.append(rm["iters"])
+        ok &= rm["status"] == 0 and rm["rse"] <= 1e-6
+        torch.cuda.synchronize(dev)
+        t_c.append(ev[0].elapsed_time(ev[1]))
+        t_m.append(ev[2].elapsed_time(ev[3]))
+        del A, b, xs
+    mean = lambda v: sum(v) / len(v)  # noqa: E731
+    out = {"m": m, "n": n, "d": d, "trials": trials, "all_converged": bool(ok),
+           "csk_it": mean(it_c), "mwrk_it": mean(it_m), "csk_ms": mean(t_c), "mwrk_ms": mean(t_m),
+           "speedup": mean(t_m) / mean(t_c)}
+    if (m, n) in PAPER:
+        pit, pmit, pcs, pms, psp = PAPER[(m, n)]
+        out["paper"] = {"csk_it": pit, "mwrk_it": pmit, "csk_s": pcs, "mwrk_s": pms, "speedup": psp}
+    return out
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--trials", type=int, default=50)
+    ap.add_argument("--m", type=int, nargs="*", default=[300000, 400000, 500000, 600000, 700000])
+    ap.add_argument("--n", type=int, nargs="*", default=[50, 100, 150])
+    args = ap.parse_args(argv)
+    import torch
+
+    from . import csk
+    csk.lib()
+    dev = torch.device("cuda", 0)
+    rows = []
+    for m in args.m:
+        for n in args.n:
+            r = run_shape(csk, torch, m, n, args.trials, dev)
+            rows.append(r)
+            print(json.dumps(r), flush=True)
+    print("\n| m | n | d | CSK IT (paper) | MWRK IT (paper) | CSK ms | MWRK ms | speedup (paper) |")
+    print("|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        p = r.get("paper", {})
+        print(f"| {r['m']} | {r['n']} | {r['d']} | {r['csk_it']:.2f} ({p.get('csk_it', '-')}) | "
+              f"{r['mwrk_it']:.2f} ({p.get('mwrk_it', '-')}) | {r['csk_ms']:.3f} | {r['mwrk_ms']:.3f} | "
+              f"{r['speedup']:.2f} ({p.get('speedup', '-')}) |")
+    return 0 if all(r["all_converged"] for r in rows) else 1
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -320,3 +320,45 @@ def test_stream_variant_idle_ctas_and_timeout(csk):
     assert info["status"] == -3
     x, info, _ = _solve(csk, s, 400, 14, grid=16, gemv_variant=3)
     assert info["status"] == 0 and info["rse"] <= 1e-6
+
+
+@pytest.mark.parametrize("pad", [0, 2])
+def test_stream_variant_fp64_unsketched_mwrk(csk, pad):
+    """FP64 MWRK on A itself through the streamed loop (16-byte chunks of two
+    doubles): the oracle's row sequence wherever the selection gap exceeds
+    1e-9, the oracle's IT, and an x within FP64 rounding of the oracle's."""
+    m, n, seed = 20000, 50, 17
+    s = synth.gaussian_system(m, n, seed, np.float64)
+    Ad = torch.zeros((m, n + pad), dtype=torch.float64, device=DEV)
+    Ad[:, :n] = _to(s.A)
+    A = Ad[:, :n]
+    ik = torch.full((20000,), -1, dtype=torch.int32, device=DEV)
+    p = csk.csk_params_default(d=0, path=csk.GEMV, gemv_variant=3, ik_log=ik.data_ptr(),
+                               ik_log_len=20000)
+    x, info = csk.csk_solve(A, _to(s.b), p, x_star=_to(s.x_star))
+    ref = oracle.mwrk(s.A, s.b, x_star=s.x_star, tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and ref.status == 0 and info["rse"] <= 1e-6
+    assert info["iters"] == ref.iters
+    _compare_prefix(ik.cpu().numpy()[:info["iters"]], ref, 1e-9)
+    err = np.sum((x.cpu().numpy() - ref.x) ** 2) / np.sum(s.x_star ** 2)
+    assert err <= 1e-20
+
+
+def test_stream_variant_fp64_sketched_matches_shared_memory_variant(csk):
+    """FP64 CSK at a Table 1 shape (d = n^2) with the sketch streamed every
+    step (variant 3) and resident in shared memory (variant 1): both follow
+    the FP64 oracle's rows up to the first near-tie, with its IT, and agree
+    with each other to FP64 rounding."""
+    m, n, d, seed = 60000, 150, 22500, 18
+    s = synth.gaussian_system(m, n, seed, np.float64)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At, bt, x_star=s.x_star, tol=1e-6, log_len=20000, nthreads=8)
+    out = []
+    for variant in (1, 3):
+        x, info, ik = _solve(csk, s, d, seed, log=20000, gemv_variant=variant)
+        assert info["status"] == 0 and info["rse"] <= 1e-6
+        assert abs(info["iters"] - ref.iters) <= 1
+        _compare_prefix(ik[:info["iters"]], ref, 1e-9)
+        out.append(x)
+    assert np.sum((out[0] - out[1]) ** 2) / np.sum(s.x_star ** 2) <= 1e-20
