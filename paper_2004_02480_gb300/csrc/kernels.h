@@ -40,16 +40,16 @@ struct SortScratch {
 size_t sort_scratch_bytes(int64_t m, int64_t d);
 void carve_sort_scratch(void* base, int64_t m, int64_t d, SortScratch* s);
 
-// Counting sort of rows by bucket (hist -> scan -> scatter -> per-bucket
-// sort).  Leaves off[d+1] and perm[m] sorted by (h(i), i).
-cudaError_t launch_bucket_sort(int64_t m, int64_t d, uint64_t seed, const SortScratch& s,
-                               cudaStream_t st);
+// Rows grouped by bucket (hist -> scan -> scatter): off[d+1], and perm_tmp[m]
+// holding each bucket's rows in no particular order.
+cudaError_t launch_bucket_group(int64_t m, int64_t d, uint64_t seed, const SortScratch& s,
+                                cudaStream_t st);
 
-// Segmented signed row sum At = S A, Bt = S B (+ FP64 row norms).
-cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int n, const void* B,
-                          int64_t ldb, int nrhs, const int32_t* perm, const int32_t* off,
-                          int d, uint64_t seed, void* At, void* Bt, double* N2,
-                          cudaStream_t st);
+// Segmented signed row sum At = S A, Bt = S B (+ FP64 row norms), after
+// launch_bucket_group; also writes perm[m], the rows sorted by (h(i), i).
+cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
+                          int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
+                          void* At, void* Bt, double* N2, cudaStream_t st);
 
 // FP64 squared row norms of a (rows x n, ld) matrix (unsketched path).
 cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int n,
