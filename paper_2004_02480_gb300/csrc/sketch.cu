@@ -246,14 +246,12 @@ __device__ __forceinline__ double seg_chunk(const T* __restrict__ src, int64_t l
 // below m / kSortCap).  Then warp w sums the column chunks w, w + W, ... of
 // the bucket's rows in that order; the FP64 row norm is combined across
 // warps in a fixed order.
-// (The 128-bit FP32 variant is held to 10 CTAs per SM: measured ~3 % faster
-// than the 9 its natural register count allows.)
 template <typename T, int V, int CPL, int U>
-__global__ void __launch_bounds__(128, (sizeof(T) == 4 && V == 4) ? 10 : 1)
+__global__ void __launch_bounds__(128)
 k_segsum(const T* __restrict__ A, int64_t lda, int n, int64_t m,
          const int32_t* __restrict__ perm_tmp, int32_t* __restrict__ perm,
          const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ At,
-         double* __restrict__ N2, const T* __restrict__ b, int64_t ldb, T* __restrict__ bt) {
+         double* __restrict__ N2) {
     __shared__ double part[4];
     __shared__ __align__(16) int32_t ubuf[kSortCap];
     __shared__ __align__(16) int32_t sbuf[kSortCap];
@@ -297,20 +295,6 @@ k_segsum(const T* __restrict__ A, int64_t lda, int n, int64_t m,
         double sq = 0.0;
         for (int c0 = warp * CW; c0 < n; c0 += W * CW)
             sq += seg_chunk<T, V, CPL, U>(A, lda, n, c0, rows, q0, q0 + cnt, seed, At + j * (int64_t)n);
-        if (b && warp == W - 1) {
-            // one right-hand side: the last warp sums it in row order (lanes
-            // load 32 rows' values, the sum takes them through shuffles)
-            T acc = T(0);
-            for (int32_t pb = q0; pb < q0 + cnt; pb += 32) {
-                const bool valid = pb + lane < q0 + cnt;
-                const int32_t row = valid ? rows[pb + lane] : 0;
-                T v = valid ? b[(int64_t)row * ldb] : T(0);
-                if (row_negative(row_hash(seed, (uint64_t)row))) v = -v;
-                const int c = min(32, q0 + cnt - pb);
-                for (int q = 0; q < c; ++q) acc += __shfl_sync(0xffffffffu, v, q);
-            }
-            if (lane == 0) bt[j] = acc;
-        }
         sq = warp_sum(sq);
         if (lane == 0) part[warp] = sq;
         __syncthreads();
@@ -435,33 +419,27 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     int64_t blocks = d;
     if (blocks > (int64_t)di.sms * 64) blocks = (int64_t)di.sms * 64;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
-    // one right-hand side is summed inside k_segsum; several by k_segsum_b
-    const void* b1 = (B && nrhs == 1) ? B : nullptr;
     // warps per bucket: one per column chunk, at most 4
     auto warps_for = [&](int cw) { int w = (n + cw - 1) / cw; return w < 1 ? 1 : (w > 4 ? 4 : w); };
     if (dtype == CSK_F32) {
         const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
         if (vec)
             k_segsum<float, 4, 1, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2,
-                (const float*)b1, ldb, (float*)Bt);
+                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2);
         else
             k_segsum<float, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2,
-                (const float*)b1, ldb, (float*)Bt);
+                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2);
     } else {
         const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
         if (vec)
             k_segsum<double, 2, 2, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2,
-                (const double*)b1, ldb, (double*)Bt);
+                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2);
         else
             k_segsum<double, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2,
-                (const double*)b1, ldb, (double*)Bt);
+                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2);
     }
     note_launches(1);
-    if (B && nrhs > 1) {
+    if (B && nrhs > 0) {
         int64_t bblocks = ((int64_t)d + 7) / 8;
         if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
         if (dtype == CSK_F32)
