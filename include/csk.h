@@ -323,6 +323,32 @@ size_t csk_solve_batched_workspace_size(const csk_system *sys, int32_t nsys);
 int csk_solve_batched(const csk_system *sys, int32_t nsys, const csk_params *params,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* ----------------------------------------------------------------------
+ * csk_synth_systems -- seeded Gaussian test systems generated on the device
+ * (no counterpart in the paper: the stand-in for systems that arrive with
+ * their data, used by the serving harness).
+ *
+ * For each system: A (m x n, row-major, leading dimension n) and X (n x nrhs,
+ * row-major) get iid N(0,1) entries, each a pure function of (seed, matrix,
+ * element index) -- a SplitMix64 counter hash and Box-Muller -- so a system's
+ * data do not depend on the other systems of the call; then B = A X
+ * (m x nrhs) accumulated in FP32 in a fixed order.  All pointers are DEVICE
+ * memory owned by the caller; nrhs <= 16.  Two launches per 32 systems; no
+ * synchronisation.  Returns CSK_EINVAL / CSK_ENOMEM on bad sizes (nothing
+ * enqueued), CSK_ECUDA if a launch fails.
+ * -------------------------------------------------------------------- */
+typedef struct {
+    int64_t m, n;
+    int32_t nrhs;
+    int32_t reserved_;
+    uint64_t seed;
+    void *A;              /* out, m x n FP32                                    */
+    void *X;              /* out, n x nrhs FP32                                 */
+    void *B;              /* out, m x nrhs FP32                                 */
+} csk_synth_system;
+
+int csk_synth_systems(const csk_synth_system *sys, int32_t count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,12 @@ class csk_host_problem(ctypes.Structure):
                 ("x_star", ctypes.c_void_p), ("x_out", ctypes.c_void_p), ("info", ctypes.c_void_p)]
 
 
+class csk_synth_system(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nrhs", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("seed", ctypes.c_uint64), ("A", ctypes.c_void_p),
+                ("X", ctypes.c_void_p), ("B", ctypes.c_void_p)]
+
+
 def lib():
     """Load libcsk.so (raises if it has not been built)."""
     global _lib
@@ -118,6 +124,8 @@ def lib():
         L.csk_solve_host_many.argtypes = [ctypes.POINTER(csk_host_problem), i32, i32,
                                           ctypes.POINTER(csk_params), P, sz, P]
         L.csk_solve_host_many.restype = ctypes.c_int
+        L.csk_synth_systems.argtypes = [ctypes.POINTER(csk_synth_system), i32, P]
+        L.csk_synth_systems.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -401,6 +409,30 @@ def csk_solve_host_many(probs: list[HostProblem], params: csk_params, *, ws: tor
     if rc < 0 and not any(q.info is not None and q.info["status"][0] == rc for q in probs):
         raise CskError(rc, "csk_solve_host_many")
     return rc
+
+
+def csk_synth_systems(systems: list[tuple], device=None) -> None:
+    """Fill seeded Gaussian systems on the device: ``systems`` holds tuples
+    (A, X, B, seed) of contiguous FP32 device tensors (m x n, n x R, m x R);
+    A and X get N(0,1) entries keyed by the seed, B = A X.  Enqueued on the
+    current stream."""
+    if not systems:
+        return
+    arr = (csk_synth_system * len(systems))()
+    dev = None
+    for q, (A, X, B, seed) in enumerate(systems):
+        dev = _check_cuda(A, X, B)
+        for t in (A, X, B):
+            if t.dtype != torch.float32 or not t.is_contiguous():
+                raise TypeError("synthetic systems are contiguous FP32")
+        m, n = A.shape
+        R = X.shape[1]
+        if tuple(X.shape) != (n, R) or tuple(B.shape) != (m, R):
+            raise ValueError("A m x n, X n x R, B m x R")
+        arr[q] = csk_synth_system(m, n, R, 0, seed & (2**64 - 1), _ptr(A), _ptr(X), _ptr(B))
+    rc = lib().csk_synth_systems(arr, len(systems), _stream(dev if device is None else device))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_synth_systems")
 
 
 def info_dict(info: np.ndarray) -> dict:

@@ -1,13 +1,14 @@
 """Continuous-batching request loop for CSK solves on one GPU.
 
 Requests (one system A x = B with 1..R right-hand sides each, Algorithm 1 per
-right-hand side) arrive over time.  The loop admits arrived requests while
-their device memory fits the HBM budget, launches each admitted group as one
-csk_solve_batched call on the next of several CUDA streams -- so work admitted
-while earlier groups are still running overlaps with them on the device --
-retires finished groups (copying X to the host and freeing their memory) as
-soon as their completion event fires, and admits waiting requests as memory
-frees up.  Latency is measured from a request's arrival to the moment its
+right-hand side) arrive over time.  Whenever one of several CUDA streams has
+no group in flight, the loop admits the arrived requests whose device memory
+fits the HBM budget (up to max_group) and launches them as one group -- their
+data generated in one call, then one csk_solve_batched call -- on that
+stream, so groups overlap on the device and, while every stream is busy,
+arrivals accumulate into larger groups.  Finished groups are retired (results
+copied to the host, memory returned to the arena) as soon as their completion
+event fires.  Latency is measured from a request's arrival to the moment its
 result is on the host.
 
 With a fixed CTA shape (``threads``) a request's arithmetic does not depend
@@ -164,7 +165,7 @@ class Server:
     """Drives Admission on a GPU: data generation, batched solves, retirement."""
 
     def __init__(self, device="cuda:0", budget_bytes: float = 120e9, threads: int = 256,
-                 max_group: int = 64, streams: int = 4, tol: float = 1e-6, keep_x: bool = False):
+                 max_group: int = 64, streams: int = 8, tol: float = 1e-6, keep_x: bool = False):
         import torch
 
         from . import csk
@@ -178,7 +179,6 @@ class Server:
         self.params = csk.csk_params_default(tol=tol, threads=threads)
         self.keep_x = keep_x
         self.launches = 0
-        self.gen = torch.Generator(device=self.dev)
 
     def _take(self, nbytes: int, held: list):
         off = self.arena.alloc(nbytes)
@@ -187,11 +187,11 @@ class Server:
         held.append((off, nbytes))
         return self.pool[off:off + ((nbytes + 3) // 4) * 4]
 
-    def _materialise(self, r: Request, held: list, info):
-        """The request's data, generated on the device from its seed (stands in
-        for a request that arrives with its matrix), in arena memory."""
-        torch = self.torch
-        f32 = torch.float32
+    def _materialise(self, r: Request, held: list, info, synth: list):
+        """Arena memory for the request's A, B, X* and X; the request's data
+        (a seeded Gaussian system, the stand-in for a request that arrives with
+        its matrix) are generated for the whole group in one call."""
+        f32 = self.torch.float32
         parts = [r.m * r.n * 4, r.m * r.nrhs * 4, r.n * r.nrhs * 4, r.n * r.nrhs * 4]
         views = []
         for nb in parts:
@@ -203,11 +203,7 @@ class Server:
         B = views[1].view(f32).view(r.m, r.nrhs)
         X = views[2].view(f32).view(r.n, r.nrhs)
         Xo = views[3].view(f32).view(r.n, r.nrhs)
-        g = self.gen
-        g.manual_seed(r.seed & ((1 << 63) - 1))
-        torch.randn((r.m, r.n), generator=g, device=self.dev, dtype=f32, out=A)
-        torch.randn((r.n, r.nrhs), generator=g, device=self.dev, dtype=f32, out=X)
-        torch.matmul(A, X, out=B)
+        synth.append((A, X, B, r.seed))
         return self.csk.BatchSystem(A=A, B=B, d=r.d, seed=r.seed, Xstar=X, Xout=Xo, info=info)
 
     def solve_group(self, group: list[Request], stream):
@@ -216,7 +212,7 @@ class Server:
         torch = self.torch
         held = []
         with torch.cuda.stream(stream):
-            systems = []
+            systems, synth = [], []
             # the group's info records sit together: one copy retires it
             rows = sum(r.nrhs for r in group)
             infos = self._take(64 * rows, held)
@@ -224,7 +220,7 @@ class Server:
             for r in group if infos is not None else ():
                 info = infos[64 * o:64 * (o + r.nrhs)].view(r.nrhs, 64)
                 o += r.nrhs
-                y = self._materialise(r, held, info)
+                y = self._materialise(r, held, info, synth)
                 if y is None:
                     break
                 systems.append(y)
@@ -235,6 +231,7 @@ class Server:
                 for off, nb in held:
                     self.arena.release(off, nb)
                 return None
+            self.csk.csk_synth_systems(synth)
             self.csk.csk_solve_batched(systems, self.params, ws=ws, sync=False)
             self.launches += 1
             ev = torch.cuda.Event()
@@ -275,34 +272,32 @@ class Server:
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        inflight = []
-        k = 0
+        # one group in flight per stream: while every stream is busy, arrivals
+        # wait in the admission queue and the next free stream takes them as
+        # one larger group (batches grow with the load)
+        inflight = {}                              # stream index -> group in flight
         while pending or self.adm.waiting or inflight:
             t = now()
             while pending and pending[0].arrival <= t:
                 self.adm.arrive(pending.popleft())
-            still = []
-            for item in inflight:
-                group, systems, held, ev = item
+            for si in list(inflight):
+                group, systems, held, ev = inflight[si]
                 if ev.query():
                     self._retire(group, systems, held, now)
                     self.adm.release(group)
-                else:
-                    still.append(item)
-            inflight = still
-            group = self.adm.admit()
+                    del inflight[si]
+            free = [si for si in range(len(self.streams)) if si not in inflight]
+            group = self.adm.admit() if free else []
             launched = None
             if group:
-                launched = self.solve_group(group, self.streams[k % len(self.streams)])
+                launched = self.solve_group(group, self.streams[free[0]])
                 if launched is None:              # arena fragmented: retry after a retire
                     self.adm.unadmit(group)
                     group = []
             if group:
                 for r in group:
                     r.t_admit = now()
-                systems, held, ev = launched
-                k += 1
-                inflight.append((group, systems, held, ev))
+                inflight[free[0]] = (group,) + launched
             elif not inflight and pending:
                 time.sleep(max(0.0, min(1e-3, pending[0].arrival - now())))
             else:
