@@ -403,6 +403,57 @@ __device__ __forceinline__ void warp_sum_rows(float (&v)[RPW]) {
         for (int u = 0; u < RPW; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
 }
 
+// Best of a warp's RPW scored rows (identical in every lane) by a tree of
+// depth log2(RPW) on monotone key codes -- NaN highest, an excluded row
+// (w < 0) lowest, else the key's bits + 1 -- with ties to the smaller row:
+// the winner of a sequential better() scan, without its serial chain.
+template <int RPW>
+__device__ __forceinline__ void best_of_rows(const float (&r)[RPW], const float (&w)[RPW],
+                                             const bool (&has)[RPW], int first_row, int row_step,
+                                             Red<float>& c) {
+    uint32_t code[RPW];
+    int32_t idx[RPW];
+    float alpha[RPW];
+#pragma unroll
+    for (int u = 0; u < RPW; ++u) {
+        const float key = r[u] * r[u] * w[u];
+        code[u] = (!has[u] || w[u] < 0.0f) ? 0u : (key != key ? 0xFFFFFFFFu : __float_as_uint(key) + 1u);
+        idx[u] = first_row + row_step * u;
+        alpha[u] = r[u] * w[u];
+    }
+#pragma unroll
+    for (int st = 1; st < RPW; st <<= 1)
+#pragma unroll
+        for (int u = 0; u + st < RPW; u += 2 * st)
+            if (code[u + st] > code[u] || (code[u + st] == code[u] && idx[u + st] < idx[u])) {
+                code[u] = code[u + st]; idx[u] = idx[u + st]; alpha[u] = alpha[u + st];
+            }
+    if (code[0] != 0u) {
+        c.key = code[0] == 0xFFFFFFFFu ? (float)NAN : __uint_as_float(code[0] - 1u);
+        c.alpha = alpha[0];
+        c.idx = idx[0];
+    }
+}
+
+// The same for either element type (codes of a double key compare as
+// doubles: NaN highest, excluded rows lowest).
+template <typename T, int N>
+__device__ __forceinline__ void best_of_rows_t(const T (&r)[N], const T (&w)[N], const bool (&has)[N],
+                                               int first_row, int row_step, Red<T>& c) {
+    if constexpr (sizeof(T) == 4) {
+        best_of_rows<N>(r, w, has, first_row, row_step, c);
+    } else {
+        // FP64: a sequential scan (the FP64 loops are compute-bound elsewhere)
+#pragma unroll
+        for (int u = 0; u < N; ++u)
+            if (has[u] && !(w[u] < T(0))) {
+                const T key = r[u] * r[u] * w[u];
+                const int j = first_row + row_step * u;
+                if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r[u] * w[u]; c.idx = j; }
+            }
+    }
+}
+
 template <int RPW, int CPL>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv_reg(IterProblem p, int R) {
@@ -464,18 +515,14 @@ k_iterate_gemv_reg(IterProblem p, int R) {
         warp_sum_rows<RPW>(dot);
         Red<float> c;
         c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
+        float res[RPW];
 #pragma unroll
-        for (int u = 0; u < RPW; ++u) {
-            if (has[u]) {
-                const float r = btu[u] - dot[u];
-                if (!(wu[u] < 0.0f)) {
-                    const float key = r * r * wu[u];
-                    const int j = r0 + warp + kWarps * u;
-                    if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r * wu[u]; c.idx = j; }
-                }
-                if (!xstar && lane == 0) c.stat += r * r;
-            }
-        }
+        for (int u = 0; u < RPW; ++u) res[u] = btu[u] - dot[u];
+        best_of_rows<RPW>(res, wu, has, r0 + warp, kWarps, c);
+        if (!xstar && lane == 0)
+#pragma unroll
+            for (int u = 0; u < RPW; ++u)
+                if (has[u]) c.stat += res[u] * res[u];
         if (xstar && warp == 0) {
             // float4 column c4 is counted by CTA c4 % G only
 #pragma unroll
@@ -729,18 +776,24 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
                 for (int u = 0; u < RPB; ++u) dot[u] += __shfl_xor_sync(0xffffffffu, dot[u], o);
+            {
+                T res[RPB], wv[RPB];
+                bool live[RPB];
 #pragma unroll
-            for (int u = 0; u < RPB; ++u) {
-                const int q = q0 + warp + kWarps * u;
-                if (q < nr) {
-                    const T r = bts[q] - dot[u];
-                    const T w = w2s[q];
-                    if (!(w < T(0))) {
-                        const T key = r * r * w;
-                        if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
-                    }
-                    if (!xstar && lane == 0) c.stat += r * r;
+                for (int u = 0; u < RPB; ++u) {
+                    const int q = q0 + warp + kWarps * u;
+                    live[u] = q < nr;
+                    res[u] = live[u] ? bts[q] - dot[u] : T(0);
+                    wv[u] = live[u] ? w2s[q] : T(-1);
                 }
+                Red<T> blk;
+                blk.key = T(-1); blk.alpha = T(0); blk.stat = T(0); blk.idx = INT_MAX;
+                best_of_rows_t<T, RPB>(res, wv, live, r0 + q0 + warp, kWarps, blk);
+                if (better(blk.key, blk.idx, c.key, c.idx)) { c.key = blk.key; c.alpha = blk.alpha; c.idx = blk.idx; }
+                if (!xstar && lane == 0)
+#pragma unroll
+                    for (int u = 0; u < RPB; ++u)
+                        if (live[u]) c.stat += res[u] * res[u];
             }
             // take over the stage of the previous block (released by now, as a rule)
             if (tid == 0 && !refill(g + nst)) stalled = 1;
