@@ -249,6 +249,28 @@ __device__ __forceinline__ T weight_of(double N) {
     return N > 0.0 ? (T)(1.0 / N) : (N == 0.0 ? T(-1) : (T)NAN);
 }
 
+// This lane's FP64 partial of a . x over columns lane, lane + 32, ... (in that
+// order), with eight loads of `a` in flight at a time.
+template <typename TA, typename TX>
+__device__ __forceinline__ double lane_dot_f64(const TA* __restrict__ a, const TX* __restrict__ x,
+                                               int n, int lane) {
+    double acc = 0.0;
+    for (int c0 = lane; c0 < n; c0 += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + 32 * u;
+            v[u] = c < n ? (double)a[c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + 32 * u;
+            if (c < n) acc = fma(v[u], (double)x[c], acc);
+        }
+    }
+    return acc;
+}
+
 // Sum of squares of a 16-byte chunk of x - x*, rounded in a fixed order (no
 // contraction left to the compiler), so the register and streamed loops
 // compute the stopping statistic identically.
@@ -882,7 +904,7 @@ int stream_rows_per_block(int cpl) {
 
 // ------------------------------------------------------------ GRAM path
 // Shared memory: r (Rpad) | w2 (Rpad) | x slice (spad) | x* slice (spad) |
-// full x for the refresh (npad)
+// full x in FP64 for the refresh (npad doubles)
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gram(IterProblem p, int R) {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -898,7 +920,7 @@ k_iterate_gram(IterProblem p, int R) {
     float* w2s = rs + Rpad;
     float* xsl = w2s + Rpad;
     float* xss = xsl + spad;
-    float* xfull = xss + spad;
+    double* xfull = reinterpret_cast<double*>(xss + spad);
     const float* At = static_cast<const float*>(p.At);
     const float* bt = static_cast<const float*>(p.bt);
     const float* x0 = static_cast<const float*>(p.x0);
@@ -932,12 +954,22 @@ k_iterate_gram(IterProblem p, int R) {
             }
             ++round;
             __threadfence();
-            for (int c = tid; c < n; c += blockDim.x) xfull[c] = __ldcg(xg + c);
+            for (int c = tid; c < n; c += blockDim.x) xfull[c] = (double)__ldcg(xg + c);
             __syncthreads();
+            // the first refresh widens this CTA's rows of At into At64 (exact),
+            // later ones read the FP64 copy: on this GPU the FP32 -> FP64
+            // conversions cost as much as the FP64 FMAs themselves
             for (int q = warp; q < nr; q += kWarps) {
                 const float* a = At + (int64_t)(r0 + q) * p.ld;
+                double* a64 = p.At64 ? p.At64 + (int64_t)(r0 + q) * n : nullptr;
                 double acc = 0.0;
-                for (int c = lane; c < n; c += 32) acc = fma((double)a[c], (double)xfull[c], acc);
+                if (k == 0 || !a64) {
+                    acc = lane_dot_f64(a, xfull, n, lane);
+                    if (a64)
+                        for (int c = lane; c < n; c += 32) a64[c] = (double)a[c];
+                } else {
+                    acc = lane_dot_f64(a64, xfull, n, lane);
+                }
                 acc = warp_sum(acc);
                 if (lane == 0) rs[q] = (float)((double)bt[r0 + q] - acc);
             }
@@ -1011,8 +1043,7 @@ k_final_rows(const T* __restrict__ At, int64_t ld, int d, int n, const T* __rest
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     double rr = 0.0, bb = 0.0, empty = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < d; j += nwarps) {
-        double s = 0.0;
-        for (int c = lane; c < n; c += 32) s = fma((double)At[j * ld + c], (double)x[c], s);
+        double s = lane_dot_f64(At + j * ld, x, n, lane);
         s = warp_sum(s);
         if (lane == 0) {
             const double r = (double)bt[j] - s;
@@ -1098,7 +1129,7 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
     cfg->rows_per_cta = R;
     if (path == CSK_RESID_GRAM) {
         cfg->cache_rows = 0;
-        cfg->smem = (size_t)(2 * Rpad + 2 * spad + npad) * 4;
+        cfg->smem = (size_t)(2 * Rpad + 2 * spad) * 4 + (size_t)npad * 8;
     } else {
         const size_t base = (size_t)(npad + 2 * Rpad + spad) * s;
         const size_t rows = (size_t)R * n * s;

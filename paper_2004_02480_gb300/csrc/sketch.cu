@@ -345,13 +345,20 @@ __global__ void k_row_norms(const T* __restrict__ A, int64_t ld, int rows, int n
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < rows;
          j += nwarps) {
+        // columns lane, lane + 32, ... in order, eight loads in flight
+        const T* a = A + j * ld;
+        const int lane = lane_id();
         double s = 0.0;
-        for (int c = lane_id(); c < n; c += 32) {
-            const double v = (double)A[j * ld + c];
-            s += v * v;
+        for (int c0 = lane; c0 < n; c0 += 32 * 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = c0 + 32 * u < n ? (double)a[c0 + 32 * u] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + 32 * u < n) s += v[u] * v[u];
         }
         s = warp_sum(s);
-        if (lane_id() == 0) N2[j] = s;
+        if (lane == 0) N2[j] = s;
     }
 }
 
