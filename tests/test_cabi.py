@@ -132,3 +132,19 @@ def test_host_many_checks_on_host(L):
     arr[1].lda = 5
     arr[0].b = None
     assert L.csk_solve_host_many(arr, 2, dt, ctypes.byref(p), fake, need, None) == csk.CSK_EINVAL
+
+
+def test_synth_systems_checks_on_host(L):
+    """csk_synth_systems rejects bad sizes before touching CUDA."""
+    fake = 256
+    ok = csk.csk_synth_system(100, 10, 4, 0, 7, fake, fake, fake)
+    arr = (csk.csk_synth_system * 2)(ok, ok)
+    assert L.csk_synth_systems(arr, 0, None) == csk.CSK_OK
+    assert L.csk_synth_systems(None, 1, None) == csk.CSK_EINVAL
+    assert L.csk_synth_systems(arr, -1, None) == csk.CSK_EINVAL
+    arr[1] = csk.csk_synth_system(100, 10, 17, 0, 7, fake, fake, fake)    # > 16 right-hand sides
+    assert L.csk_synth_systems(arr, 2, None) == csk.CSK_EINVAL
+    arr[1] = csk.csk_synth_system(100, 10, 4, 0, 7, None, fake, fake)
+    assert L.csk_synth_systems(arr, 2, None) == csk.CSK_EINVAL
+    arr[1] = csk.csk_synth_system(0, 10, 4, 0, 7, fake, fake, fake)
+    assert L.csk_synth_systems(arr, 2, None) == csk.CSK_EINVAL
