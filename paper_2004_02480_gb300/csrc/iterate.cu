@@ -250,20 +250,20 @@ __device__ __forceinline__ T weight_of(double N) {
 }
 
 // This lane's FP64 partial of a . x over columns lane, lane + 32, ... (in that
-// order), with eight loads of `a` in flight at a time.
+// order), with sixteen loads of `a` in flight at a time.
 template <typename TA, typename TX>
 __device__ __forceinline__ double lane_dot_f64(const TA* __restrict__ a, const TX* __restrict__ x,
                                                int n, int lane) {
     double acc = 0.0;
-    for (int c0 = lane; c0 < n; c0 += 32 * 8) {
-        double v[8];
+    for (int c0 = lane; c0 < n; c0 += 32 * 16) {
+        double v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int c = c0 + 32 * u;
             v[u] = c < n ? (double)a[c] : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int c = c0 + 32 * u;
             if (c < n) acc = fma(v[u], (double)x[c], acc);
         }
