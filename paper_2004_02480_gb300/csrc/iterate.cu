@@ -40,7 +40,7 @@ namespace {
 constexpr int kIterThreads = 256;
 constexpr int kWarps = kIterThreads / 32;
 constexpr int64_t kDefaultSpin = 1ll << 22;
-constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP)
+constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP); transpose_sum8 relies on 8
 
 // ----------------------------------------------------- candidate algebra
 // Larger key wins; equal keys -> smaller row (first maximiser); NaN keys win
@@ -284,6 +284,36 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
     return __fma_rn(t[1], t[1], __dmul_rn(t[0], t[0]));
 }
 
+// Sums of a warp's 8 rows (acc[u] = this lane's partial of row u) by a
+// transposed butterfly: each level halves the rows a lane carries, so the 8
+// sums cost 9 shuffles and adds instead of 40, and lane l ends with the sum of
+// row 4 b4 + 2 b3 + b2 (bits of l).  Every level adds the same pairs as the
+// xor butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
+// warp_sum of its row.
+template <typename T>
+__device__ __forceinline__ T transpose_sum8(const T (&a)[8], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    T v4[4], v2[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T send = h16 ? a[i] : a[i + 4];
+        const T keep = h16 ? a[i + 4] : a[i];
+        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const T send = h8 ? v4[i] : v4[i + 2];
+        const T keep = h8 ? v4[i + 2] : v4[i];
+        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const T send = h4 ? v2[0] : v2[1];
+    const T keep = h4 ? v2[1] : v2[0];
+    T v = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
 template <typename T>
@@ -365,18 +395,18 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                         if (u < myrows) acc[u] = fma(Abase[(int64_t)(base + u * kWarps) * lda + col], xv, acc[u]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kRowsPerWarp; ++u) {
-                if (u < myrows) {
-                    const int q = base + u * kWarps;
-                    const T r = bts[q] - warp_sum(acc[u]);
-                    const T w = w2s[q];
-                    if (!(w < T(0))) {
-                        const T key = r * r * w;
-                        if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
-                    }
-                    if (!xstar && lane == 0) c.stat += r * r;
+            // lane l ends with row u(l)'s sum, bit for bit the warp_sum of that row
+            const T sum = transpose_sum8(acc, lane);
+            const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && u < myrows) {
+                const int q = base + u * kWarps;
+                const T r = bts[q] - sum;
+                const T w = w2s[q];
+                if (!(w < T(0))) {
+                    const T key = r * r * w;
+                    if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
                 }
+                if (!xstar) c.stat += r * r;
             }
         }
         if (xstar)
@@ -384,7 +414,7 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 const T t = xs[col] - xss[col - c0];
                 c.stat += t * t;
             }
-        c = block_reduce_wu(c, sh, par);
+        c = block_reduce(c, sh, par);    // candidates differ across lanes
         // Phase B
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
