@@ -40,7 +40,7 @@ namespace {
 constexpr int kIterThreads = 256;
 constexpr int kWarps = kIterThreads / 32;
 constexpr int64_t kDefaultSpin = 1ll << 22;
-constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP); transpose_sum8 relies on 8
+constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP; 1, 2, 4 or 8)
 
 // ----------------------------------------------------- candidate algebra
 // Larger key wins; equal keys -> smaller row (first maximiser); NaN keys win
@@ -284,35 +284,51 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
     return __fma_rn(t[1], t[1], __dmul_rn(t[0], t[0]));
 }
 
-// Sums of a warp's 8 rows (acc[u] = this lane's partial of row u) by a
-// transposed butterfly: each level halves the rows a lane carries, so the 8
-// sums cost 9 shuffles and adds instead of 40, and lane l ends with the sum of
-// row 4 b4 + 2 b3 + b2 (bits of l).  Every level adds the same pairs as the
-// xor butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
+// Sums of a warp's N rows (N = 1, 2, 4, 8; a[u] = this lane's partial of row
+// u) by a transposed butterfly: each of the first log2(N) levels halves the
+// rows a lane carries, so the N sums cost 5 + N - 1 shuffles and adds instead
+// of 5 N, and lane l ends with the sum of row transpose_row<N>(l) (lane bits
+// 4, 3, 2 from the top).  Every level adds the same pairs as the xor
+// butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
 // warp_sum of its row.
-template <typename T>
-__device__ __forceinline__ T transpose_sum8(const T (&a)[8], int lane) {
-    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-    T v4[4], v2[2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const T send = h16 ? a[i] : a[i + 4];
-        const T keep = h16 ? a[i + 4] : a[i];
-        v4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const T send = h8 ? v4[i] : v4[i + 2];
-        const T keep = h8 ? v4[i + 2] : v4[i];
-        v2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    const T send = h4 ? v2[0] : v2[1];
-    const T keep = h4 ? v2[1] : v2[0];
-    T v = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
+template <int N>
+__device__ __forceinline__ int transpose_row(int lane) {
+    return N == 8 ? ((lane >> 2) & 7) : N == 4 ? ((lane >> 3) & 3) : N == 2 ? ((lane >> 4) & 1) : 0;
 }
+
+// The lane of each group holding one row that reports it (lowest free bits 0).
+template <int N>
+__device__ __forceinline__ bool transpose_rep(int lane) {
+    return (lane & (32 / N - 1)) == 0;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T transpose_sum(const T (&a)[N], int lane) {
+    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N = 1, 2, 4 or 8");
+    T v[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) v[u] = a[u];
+    int off = 16;
+#pragma unroll
+    for (int m = N; m > 1; m >>= 1, off >>= 1) {
+        const bool hi = lane & off;
+#pragma unroll
+        for (int i = 0; i < m / 2; ++i) {
+            const T send = hi ? v[i] : v[i + m / 2];
+            const T keep = hi ? v[i + m / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    T r = v[0];
+#pragma unroll
+    for (; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    return r;
+}
+
+template <int R>
+struct Pow2Rows {   // smallest of 1, 2, 4, 8 holding R rows
+    static constexpr int N = R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8;
+};
 
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
@@ -396,9 +412,9 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 }
             }
             // lane l ends with row u(l)'s sum, bit for bit the warp_sum of that row
-            const T sum = transpose_sum8(acc, lane);
-            const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-            if ((lane & 3) == 0 && u < myrows) {
+            const T sum = transpose_sum<T, kRowsPerWarp>(acc, lane);
+            const int u = transpose_row<kRowsPerWarp>(lane);
+            if (transpose_rep<kRowsPerWarp>(lane) && u < myrows) {
                 const int q = base + u * kWarps;
                 const T r = bts[q] - sum;
                 const T w = w2s[q];
@@ -447,65 +463,6 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
 // CTA reduction.  The projection is applied by every warp to its own copy
 // of x (identical arithmetic everywhere); float4 column c4 of the
 // ||x - x*||^2 statistic is counted by CTA c4 % grid alone.
-template <int RPW>
-__device__ __forceinline__ void warp_sum_rows(float (&v)[RPW]) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int u = 0; u < RPW; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
-}
-
-// Best of a warp's RPW scored rows (identical in every lane) by a tree of
-// depth log2(RPW) on monotone key codes -- NaN highest, an excluded row
-// (w < 0) lowest, else the key's bits + 1 -- with ties to the smaller row:
-// the winner of a sequential better() scan, without its serial chain.
-template <int RPW>
-__device__ __forceinline__ void best_of_rows(const float (&r)[RPW], const float (&w)[RPW],
-                                             const bool (&has)[RPW], int first_row, int row_step,
-                                             Red<float>& c) {
-    uint32_t code[RPW];
-    int32_t idx[RPW];
-    float alpha[RPW];
-#pragma unroll
-    for (int u = 0; u < RPW; ++u) {
-        const float key = r[u] * r[u] * w[u];
-        code[u] = (!has[u] || w[u] < 0.0f) ? 0u : (key != key ? 0xFFFFFFFFu : __float_as_uint(key) + 1u);
-        idx[u] = first_row + row_step * u;
-        alpha[u] = r[u] * w[u];
-    }
-#pragma unroll
-    for (int st = 1; st < RPW; st <<= 1)
-#pragma unroll
-        for (int u = 0; u + st < RPW; u += 2 * st)
-            if (code[u + st] > code[u] || (code[u + st] == code[u] && idx[u + st] < idx[u])) {
-                code[u] = code[u + st]; idx[u] = idx[u + st]; alpha[u] = alpha[u + st];
-            }
-    if (code[0] != 0u) {
-        c.key = code[0] == 0xFFFFFFFFu ? (float)NAN : __uint_as_float(code[0] - 1u);
-        c.alpha = alpha[0];
-        c.idx = idx[0];
-    }
-}
-
-// The same for either element type (codes of a double key compare as
-// doubles: NaN highest, excluded rows lowest).
-template <typename T, int N>
-__device__ __forceinline__ void best_of_rows_t(const T (&r)[N], const T (&w)[N], const bool (&has)[N],
-                                               int first_row, int row_step, Red<T>& c) {
-    if constexpr (sizeof(T) == 4) {
-        best_of_rows<N>(r, w, has, first_row, row_step, c);
-    } else {
-        // FP64: a sequential scan (the FP64 loops are compute-bound elsewhere)
-#pragma unroll
-        for (int u = 0; u < N; ++u)
-            if (has[u] && !(w[u] < T(0))) {
-                const T key = r[u] * r[u] * w[u];
-                const int j = first_row + row_step * u;
-                if (better(key, j, c.key, c.idx)) { c.key = key; c.alpha = r[u] * w[u]; c.idx = j; }
-            }
-    }
-}
-
 template <int RPW, int CPL>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv_reg(IterProblem p, int R) {
@@ -564,17 +521,30 @@ k_iterate_gemv_reg(IterProblem p, int R) {
             }
             dot[u] = acc;
         }
-        warp_sum_rows<RPW>(dot);
+        // each lane ends with one row's residual and scores it; the CTA
+        // reduction picks the best of all lanes
+        constexpr int N = Pow2Rows<RPW>::N;
+        float part[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) part[u] = u < RPW ? dot[u] : 0.0f;
+        const float sum = transpose_sum<float, N>(part, lane);
+        const int u = transpose_row<N>(lane);
+        float bt_u = 0.0f, w_u = -1.0f;
+        bool has_u = false;
+#pragma unroll
+        for (int v = 0; v < RPW; ++v)
+            if (v == u) { bt_u = btu[v]; w_u = wu[v]; has_u = has[v]; }
         Red<float> c;
         c.key = -1.0f; c.alpha = 0.0f; c.stat = 0.0f; c.idx = INT_MAX;
-        float res[RPW];
-#pragma unroll
-        for (int u = 0; u < RPW; ++u) res[u] = btu[u] - dot[u];
-        best_of_rows<RPW>(res, wu, has, r0 + warp, kWarps, c);
-        if (!xstar && lane == 0)
-#pragma unroll
-            for (int u = 0; u < RPW; ++u)
-                if (has[u]) c.stat += res[u] * res[u];
+        if (transpose_rep<N>(lane) && has_u) {
+            const float r = bt_u - sum;
+            if (!(w_u < 0.0f)) {
+                c.key = r * r * w_u;
+                c.alpha = r * w_u;
+                c.idx = r0 + warp + kWarps * u;
+            }
+            if (!xstar) c.stat += r * r;
+        }
         if (xstar && warp == 0) {
             // float4 column c4 is counted by CTA c4 % G only
 #pragma unroll
@@ -586,7 +556,7 @@ k_iterate_gemv_reg(IterProblem p, int R) {
                 }
             }
         }
-        c = block_reduce_wu(c, sh, par);
+        c = block_reduce(c, sh, par);    // candidates differ across lanes
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
@@ -824,28 +794,21 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int u = 0; u < RPB; ++u) dot[u] += __shfl_xor_sync(0xffffffffu, dot[u], o);
             {
-                T res[RPB], wv[RPB];
-                bool live[RPB];
-#pragma unroll
-                for (int u = 0; u < RPB; ++u) {
-                    const int q = q0 + warp + kWarps * u;
-                    live[u] = q < nr;
-                    res[u] = live[u] ? bts[q] - dot[u] : T(0);
-                    wv[u] = live[u] ? w2s[q] : T(-1);
+                // lane l ends with row transpose_row(l) of the block and
+                // keeps its own running candidate across the blocks
+                const T sum = transpose_sum<T, RPB>(dot, lane);
+                const int u = transpose_row<RPB>(lane);
+                const int q = q0 + warp + kWarps * u;
+                if (transpose_rep<RPB>(lane) && q < nr) {
+                    const T r = bts[q] - sum;
+                    const T w = w2s[q];
+                    if (!(w < T(0))) {
+                        const T key = r * r * w;
+                        if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
+                    }
+                    if (!xstar) c.stat += r * r;
                 }
-                Red<T> blk;
-                blk.key = T(-1); blk.alpha = T(0); blk.stat = T(0); blk.idx = INT_MAX;
-                best_of_rows_t<T, RPB>(res, wv, live, r0 + q0 + warp, kWarps, blk);
-                if (better(blk.key, blk.idx, c.key, c.idx)) { c.key = blk.key; c.alpha = blk.alpha; c.idx = blk.idx; }
-                if (!xstar && lane == 0)
-#pragma unroll
-                    for (int u = 0; u < RPB; ++u)
-                        if (live[u]) c.stat += res[u] * res[u];
             }
             // take over the stage of the previous block (released by now, as a rule)
             if (tid == 0 && !refill(g + nst)) stalled = 1;
@@ -868,7 +831,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 }
             }
         }
-        c = block_reduce_wu(c, sh, par);
+        c = block_reduce(c, sh, par);    // candidates differ across lanes
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
