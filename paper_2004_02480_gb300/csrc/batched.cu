@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "reduce.cuh"
 
 namespace csk {
 
@@ -51,50 +52,13 @@ __global__ void k_write_table(TableChunk c, BatchSys* table) {
     if (i < c.count) table[c.first + i] = c.e[i];
 }
 
-template <typename T>
-struct Red {
-    T key, alpha, stat;
-    int32_t idx;
-};
-
-__device__ __forceinline__ bool better(float ka, int32_t ia, float kb, int32_t ib) {
-    const bool na = ka != ka, nb = kb != kb;
-    if (na != nb) return na;
-    if (na) return ia < ib;
-    return ka > kb || (ka == kb && ia < ib);
-}
-
-__device__ __forceinline__ void warp_reduce(Red<float>& c) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float k2 = __shfl_xor_sync(0xffffffffu, c.key, o);
-        const float a2 = __shfl_xor_sync(0xffffffffu, c.alpha, o);
-        const int32_t i2 = __shfl_xor_sync(0xffffffffu, c.idx, o);
-        c.stat += __shfl_xor_sync(0xffffffffu, c.stat, o);
-        if (better(k2, i2, c.key, c.idx)) { c.key = k2; c.alpha = a2; c.idx = i2; }
-    }
-}
-
 constexpr int kMaxWarps = 32;
 
 struct BatchShared {
-    Red<float> buf[2][kMaxWarps];
+    RedShared<float, kMaxWarps> red;
     double dbuf[kMaxWarps];
     int unit;
 };
-
-__device__ __forceinline__ Red<float> block_reduce(Red<float> c, BatchShared& sh, int& par) {
-    warp_reduce(c);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (lane == 0) sh.buf[par][warp] = c;
-    __syncthreads();
-    Red<float> r;
-    if (lane < nw) r = sh.buf[par][lane];
-    else { r.key = -1.0f; r.alpha = 0.0f; r.stat = 0.0f; r.idx = INT_MAX; }
-    par ^= 1;
-    warp_reduce(r);
-    return r;
-}
 
 __device__ __forceinline__ double block_sum_f64(double v, BatchShared& sh) {
     v = warp_sum(v);
@@ -248,7 +212,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
                 }
             }
         }
-        c = block_reduce(c, sh, par);
+        c = block_reduce(c, sh.red, par);
         if (c.stat <= threshold) { status = CSK_OK; break; }
         if (k >= max_iter) { status = CSK_MAXITER; break; }
         if (c.key != c.key || c.key < 0.0f) { status = CSK_ENUMERIC; break; }

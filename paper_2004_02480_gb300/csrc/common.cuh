@@ -43,34 +43,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// --------------------------------------------------- argmax candidates
-// Selection key of Algorithm 1 (squared, weighted): key = r_j^2 / ||At_j||^2.
-// Order: larger key wins; equal keys -> smaller row index (first maximiser).
-// NaN keys win over everything so a numerical failure propagates to the
-// decision every CTA takes.
-struct Cand {
-    double key;     // -1 for "no candidate" (zero row / empty range)
-    double alpha;   // step length r_j / ||At_j||^2 of this row
-    int32_t idx;
-};
-
-__device__ __forceinline__ bool cand_better(double ka, int32_t ia, double kb, int32_t ib) {
-    const bool na = ka != ka, nb = kb != kb;
-    if (na != nb) return na;
-    if (na) return ia < ib;
-    return ka > kb || (ka == kb && ia < ib);
-}
-
-__device__ __forceinline__ void warp_argmax(double& key, double& alpha, int32_t& idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        double a2 = __shfl_xor_sync(0xffffffffu, alpha, o);
-        int32_t i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (cand_better(k2, i2, key, idx)) { key = k2; alpha = a2; idx = i2; }
-    }
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
