@@ -77,7 +77,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
     t = (a - (s - bb)) + (b - bb);
 }
 
-constexpr int kGChunk = 16;    // G-row values per thread in flight at once
+constexpr int kGChunk = 8;     // G-row values per thread per chunk (two chunks in flight)
 constexpr int kXChunk = 4;     // At-row values per thread in flight at once
 
 // Monotone code of a selection key: NaN highest (a numerical failure must
@@ -162,28 +162,52 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
         uint32_t bc[4] = {0u, 0u, 0u, 0u};
         int32_t bi[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
         float ba[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // G[idx, :] in chunks of kGChunk values per thread, the next chunk's
+        // loads issued before the current chunk is scored
+        float gv[kGChunk];
+#pragma unroll
+        for (int q = 0; q < kGChunk; ++q) {
+            const int j = q * nt + tid;
+            gv[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
+        }
         for (int base = 0; base < d; base += kGChunk * nt) {
-            float gv[kGChunk];
+            float gn[kGChunk];
+            const int nb = base + kGChunk * nt;
+#pragma unroll
+            for (int q = 0; q < kGChunk; ++q) {
+                const int j = nb + q * nt + tid;
+                gn[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
+            }
+            // the chunk's r and weights are read before any r is written back,
+            // so the rows' shared-memory accesses do not serialise
+            float rv[kGChunk], wv[kGChunk];
 #pragma unroll
             for (int q = 0; q < kGChunk; ++q) {
                 const int j = base + q * nt + tid;
-                gv[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
+                rv[q] = j < d ? rs[j] : 0.0f;
+                wv[q] = j < d ? w2s[j] : -1.0f;
             }
 #pragma unroll
             for (int q = 0; q < kGChunk; ++q) {
                 const int j = base + q * nt + tid;
                 if (j < d) {
-                    float r = rs[j];
-                    if (grow) {
-                        r = (j == idx) ? 0.0f : fmaf(-alpha, gv[q], r);
-                        rs[j] = r;
-                    }
-                    const float w = w2s[j];
+                    float r = rv[q];
+                    if (grow) r = (j == idx) ? 0.0f : fmaf(-alpha, gv[q], r);
+                    rv[q] = r;
+                    const float w = wv[q];
                     const uint32_t code = (w < 0.0f) ? 0u : key_code(r * r * w);
                     if (code > bc[q & 3]) { bc[q & 3] = code; bi[q & 3] = j; ba[q & 3] = r * w; }
                     if (!xstar) c.stat += r * r;
                 }
             }
+            if (grow)
+#pragma unroll
+                for (int q = 0; q < kGChunk; ++q) {
+                    const int j = base + q * nt + tid;
+                    if (j < d) rs[j] = rv[q];
+                }
+#pragma unroll
+            for (int q = 0; q < kGChunk; ++q) gv[q] = gn[q];
         }
 #pragma unroll
         for (int a = 1; a < 4; ++a)
