@@ -50,15 +50,10 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Slot through which a CTA publishes its candidate for one exchange round.
-// `stamp` is written last with release semantics; a reader that observes the
-// stamp of the round it waits for (acquire) also observes the payload.
+// Unit of the exchange mailboxes (32 bytes): an FP32 round stores four
+// stamped 64-bit words per slot, an FP64 round eight (two units).
 struct __align__(32) Slot {
-    double key;
-    double alpha;
-    double stat;      // partial stopping statistic (||x-x*||^2 or ||r||^2)
-    int32_t idx;
-    uint32_t stamp;
+    uint64_t w[4];
 };
 
 // Status written into csk_info by the first CTA that fails.

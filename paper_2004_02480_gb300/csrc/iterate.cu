@@ -101,34 +101,59 @@ __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>
     return true;
 }
 
-// FP64: payload, then a release-stamped word; readers acquire the stamp.
+// FP64: a slot is eight 64-bit words (64 bytes), each carrying the round
+// stamp in its high half beside 32 payload bits: key, step length and
+// statistic as two halves each, then the row.  As for FP32, one relaxed load
+// of each word both detects the new round and delivers the data, and a
+// reader that sees the stamp on all eight words has a consistent payload.
+__device__ __forceinline__ uint64_t* mailbox64(Slot* slots, uint32_t round, int dest, int src) {
+    const int G = gridDim.x;
+    return reinterpret_cast<uint64_t*>(slots) + ((((size_t)(round & 1u) * G + dest) * G + src) << 3);
+}
+
 __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<double>& c,
                                          int64_t spin_limit, int fault_inject, csk_info* info,
                                          RedShared<double>& sh, int& par) {
     const int G = gridDim.x, b = blockIdx.x;
-    if (!(fault_inject && b == 0))
+    const uint64_t stamp = (uint64_t)(round + 1u) << 32;
+    if (!(fault_inject && b == 0)) {
+        const uint64_t kb = (uint64_t)__double_as_longlong(c.key);
+        const uint64_t ab = (uint64_t)__double_as_longlong(c.alpha);
+        const uint64_t sb = (uint64_t)__double_as_longlong(c.stat);
         for (int t = threadIdx.x; t < G; t += blockDim.x) {
-            Slot* w = mailbox(slots, round, t, b);
-            w->key = c.key;
-            w->alpha = c.alpha;
-            w->stat = c.stat;
-            w->idx = c.idx;
-            st_release_u32(&w->stamp, round + 1u);
+            uint64_t* w = mailbox64(slots, round, t, b);
+            st_relaxed_v2(w, stamp | (kb >> 32), stamp | (kb & 0xFFFFFFFFull));
+            st_relaxed_v2(w + 2, stamp | (ab >> 32), stamp | (ab & 0xFFFFFFFFull));
+            st_relaxed_v2(w + 4, stamp | (sb >> 32), stamp | (sb & 0xFFFFFFFFull));
+            st_relaxed_v2(w + 6, stamp | (uint32_t)c.idx, stamp);
         }
+    }
     Red<double> g;
     g.key = -1.0; g.alpha = 0.0; g.stat = 0.0; g.idx = INT_MAX;
     int timed_out = 0;
+    const uint64_t hi = stamp >> 32;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
-        Slot* w = mailbox(slots, round, b, t);
+        const uint64_t* w = mailbox64(slots, round, b, t);
+        uint64_t v[8];
         int64_t spins = 0;
-        while (ld_acquire_u32(&w->stamp) != round + 1u) {
+        for (;;) {
+            ld_relaxed_v2(w, v[0], v[1]);
+            ld_relaxed_v2(w + 2, v[2], v[3]);
+            ld_relaxed_v2(w + 4, v[4], v[5]);
+            ld_relaxed_v2(w + 6, v[6], v[7]);
+            bool all = true;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) all &= (v[q] >> 32) == hi;
+            if (all) break;
             if (++spins > spin_limit) { timed_out = 1; break; }
         }
         if (timed_out) break;
-        const double k2 = __ldcg(&w->key);
-        const int32_t i2 = __ldcg(&w->idx);
-        g.stat += __ldcg(&w->stat);
-        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = __ldcg(&w->alpha); g.idx = i2; }
+        const double k2 = __longlong_as_double((long long)((v[0] << 32) | (v[1] & 0xFFFFFFFFull)));
+        const double a2 = __longlong_as_double((long long)((v[2] << 32) | (v[3] & 0xFFFFFFFFull)));
+        const double s2 = __longlong_as_double((long long)((v[4] << 32) | (v[5] & 0xFFFFFFFFull)));
+        const int32_t i2 = (int32_t)(uint32_t)v[6];
+        g.stat += s2;
+        if (better(k2, i2, g.key, g.idx)) { g.key = k2; g.alpha = a2; g.idx = i2; }
     }
     if (__syncthreads_or(timed_out)) {
         if (threadIdx.x == 0) set_status_once(info, CSK_ETIMEOUT);

@@ -60,9 +60,10 @@ cudaError_t launch_norm2(int dtype, const void* v, int64_t len, double* out, cud
 
 // -------------------------------------------------------------- iterate
 // Largest CTA count of the persistent loop; the exchange mailboxes take
-// 2 * grid * grid * sizeof(Slot) bytes.
+// 2 * grid * grid slots of 64 bytes (FP32 rounds use the first half of the
+// area, 32-byte slots; FP64 rounds all of it).
 constexpr int kMaxIterGrid = 320;
-inline size_t exchange_bytes(int grid) { return (size_t)2 * grid * grid * 32; }
+inline size_t exchange_bytes(int grid) { return (size_t)2 * grid * grid * 64; }
 struct IterConfig {
     int grid = 0;           // CTAs
     int threads = 256;

@@ -56,6 +56,26 @@ __device__ __forceinline__ void warp_reduce(Red<float>& c) {
     c.stat = warp_sum(c.stat);
 }
 
+// FP64 warp argmax with integer comparisons: non-negative doubles order as
+// their bit patterns, so the key becomes a monotone 64-bit code (NaN highest,
+// "no candidate" lowest) compared on the integer pipe -- this GPU runs FP64
+// at 1/64 of the FP32 rate.  Same ordering as better(); the statistic is
+// summed with the same shuffle tree as before.
+__device__ __forceinline__ void warp_reduce(Red<double>& c) {
+    uint64_t code = c.key != c.key ? ~0ull
+                                   : (c.key < 0.0 ? 0ull : (uint64_t)__double_as_longlong(c.key) + 1ull);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t c2 = __shfl_xor_sync(0xffffffffu, code, o);
+        const double a2 = __shfl_xor_sync(0xffffffffu, c.alpha, o);
+        const int32_t i2 = __shfl_xor_sync(0xffffffffu, c.idx, o);
+        c.stat += __shfl_xor_sync(0xffffffffu, c.stat, o);
+        if (c2 > code || (c2 == code && i2 < c.idx)) { code = c2; c.alpha = a2; c.idx = i2; }
+    }
+    c.key = code == ~0ull ? (double)NAN
+          : code == 0ull ? -1.0 : __longlong_as_double((long long)(code - 1ull));
+}
+
 // CTA-wide reduction with a single barrier: warps post their partial results
 // in one of two shared buffers (alternating between calls), then every warp
 // reduces the posted partials itself, so all threads end with the same bits.
