@@ -114,6 +114,9 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+LOOP_SOURCES = ("iterate.cu", "common.cuh", "reduce.cuh", "async.cuh")
+
+
 def _source_hash(*files):
     h = hashlib.sha256()
     for f in files:
@@ -530,7 +533,7 @@ def main():
     achieved = it_bytes / (it_ms * 1e-3) / 1e9
     sk_ms = float(np.mean(st_sketch))
     sk_gbs = sketch_bytes(M, N_COLS, D) / (sk_ms * 1e-3) / 1e9
-    src = _source_hash("paper_2004_02480_gb300/csrc/iterate.cu", "paper_2004_02480_gb300/csrc/common.cuh")
+    src = _source_hash(*(f"paper_2004_02480_gb300/csrc/{f}" for f in LOOP_SOURCES))
     loop_kernel = LOOP_KERNELS.get(tuned["gemv_variant"], "k_iterate_gemv")
     traffic = _traffic(loop_kernel + "_100000x500_d5000", src)
 
