@@ -231,6 +231,15 @@ def run_c1(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     r = csk.read_info(info)
+    # stage breakdown of one more solve (events between the stages)
+    ev = _events(torch, 5)
+    csk.set_stage_events(p, ev)
+    stages = []
+    for _ in range(5):
+        csk.csk_solve(A, b, p, x_star=xs, x_out=x, info=info, ws=ws, sync=False)
+        torch.cuda.synchronize()
+        stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    st = np.median(np.array(stages), axis=0)
     ref = oracle.csk(s.A, s.b, 500, 0, x_star=s.x_star)
     print(json.dumps({
         "metric": "time-to-RSE<=1e-6 (ms), plain CSK FP64, A 2000x50, d=500", "value": ms,
@@ -238,7 +247,10 @@ def run_c1(args):
         "dtype": "f64", "data": "synthetic (seeded N(0,1))",
         "config": {"workload": "plain CSK FP64: A 2000x50 iid N(0,1), x* iid N(0,1), b=Ax*, d=500, "
                                "x0=0, stop at RES<=1e-6", "grid": r["grid"]},
-        "iters": r["iters"], "oracle_iters": ref.iters, "rse": r["rse"], "status": r["status"]}),
+        "iters": r["iters"], "oracle_iters": ref.iters, "rse": r["rse"], "status": r["status"],
+        "breakdown": {"setup_ms": float(st[0]), "sketch_ms": float(st[1]), "iterate_ms": float(st[2]),
+                      "check_ms": float(st[3]),
+                      "us_per_step": 1e3 * float(st[2]) / (r["iters"] + 1)}}),
         flush=True)
     return 0
 

@@ -42,7 +42,7 @@ __global__ void k_info_init(csk_info* info, int path, int rows, int grid) {
 //   G (d x d, GRAM) | Gram operand scratch (GRAM)
 
 struct SolveLayout {
-    size_t sort, At, bt, N2, norm, slots, xg, part, G, gscr, At64, total;
+    size_t sort, At, bt, N2, norm, slots, xg, part, G, gscr, total;
 };
 
 void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLayout* L) {
@@ -59,7 +59,6 @@ void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLay
     L->part = o;  o += align256(final_check_partials((int)rows) * 8);
     L->G = o;     o += path == CSK_RESID_GRAM ? align256((size_t)rows * gram_ld((int)rows) * 4) : 0;
     L->gscr = o;  o += path == CSK_RESID_GRAM ? align256(gram_scratch_bytes((int)rows, (int)n)) : 0;
-    L->At64 = o;  o += path == CSK_RESID_GRAM ? align256((size_t)rows * n * 8) : 0;
     L->total = o;
 }
 
@@ -205,7 +204,6 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     p.slots = slots;
     p.xg = w + L.xg;
     p.G = G; p.ldg = gram_ld(rows);
-    p.At64 = path == CSK_RESID_GRAM ? reinterpret_cast<double*>(w + L.At64) : nullptr;
     p.refresh_every = params->refresh_every;
     p.ik_log = params->ik_log; p.ik_log_len = params->ik_log_len;
     p.x_log = params->x_log; p.x_log_len = params->x_log_len;

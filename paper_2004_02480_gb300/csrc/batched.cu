@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "fp64.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -79,6 +80,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
 
 constexpr int kGChunk = 8;     // G-row values per thread per chunk (two chunks in flight)
 constexpr int kXChunk = 4;     // At-row values per thread in flight at once
+constexpr int kRefreshRows = 4;   // rows a warp sums at once in the FP64 refresh
 
 // Monotone code of a selection key: NaN highest (a numerical failure must
 // reach the decision), "no candidate" (a zero row) lowest, otherwise the
@@ -131,12 +133,12 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
                 idx = -1;
             }
             __syncthreads();
-            for (int j = warp; j < d; j += nw) {
-                const float* a = S.At + (int64_t)j * n;
-                double acc = 0.0;
-                for (int c = lane; c < n; c += 32) acc = fma((double)a[c], (double)xs[c], acc);
-                acc = warp_sum(acc);
-                if (lane == 0) rs[j] = (float)((double)S.Bt[(int64_t)j * R + rhs] - acc);
+            for (int j0 = warp * kRefreshRows; j0 < d; j0 += nw * kRefreshRows) {
+                const int m = min(kRefreshRows, d - j0);
+                const double acc = warp_rows_dot_f64<kRefreshRows>(S.At + (int64_t)j0 * n, n, m, xs, n, lane);
+                const int u = transpose_row<kRefreshRows>(lane);
+                if (transpose_rep<kRefreshRows>(lane) && u < m)
+                    rs[j0 + u] = (float)(widen(S.Bt[(int64_t)(j0 + u) * R + rhs]) - acc);
             }
             __syncthreads();
         }

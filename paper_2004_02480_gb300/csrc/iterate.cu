@@ -31,6 +31,7 @@
 
 #include "async.cuh"
 #include "common.cuh"
+#include "fp64.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -42,6 +43,7 @@ constexpr int kIterThreads = 256;
 constexpr int kWarps = kIterThreads / 32;
 constexpr int64_t kDefaultSpin = 1ll << 22;
 constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP; 1, 2, 4 or 8)
+constexpr int kRefreshRows = 4;          // rows a warp sums at once in the FP64 refresh
 
 // ---------------------------------------------------------- exchanges
 // Mailboxes: bank (round parity) x destination CTA x source CTA, 32 bytes
@@ -224,52 +226,6 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
     return __fma_rn(t[1], t[1], __dmul_rn(t[0], t[0]));
 }
 
-// Sums of a warp's N rows (N = 1, 2, 4, 8; a[u] = this lane's partial of row
-// u) by a transposed butterfly: each of the first log2(N) levels halves the
-// rows a lane carries, so the N sums cost 5 + N - 1 shuffles and adds instead
-// of 5 N, and lane l ends with the sum of row transpose_row<N>(l) (lane bits
-// 4, 3, 2 from the top).  Every level adds the same pairs as the xor
-// butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
-// warp_sum of its row.
-template <int N>
-__device__ __forceinline__ int transpose_row(int lane) {
-    return N == 8 ? ((lane >> 2) & 7) : N == 4 ? ((lane >> 3) & 3) : N == 2 ? ((lane >> 4) & 1) : 0;
-}
-
-// The lane of each group holding one row that reports it (lowest free bits 0).
-template <int N>
-__device__ __forceinline__ bool transpose_rep(int lane) {
-    return (lane & (32 / N - 1)) == 0;
-}
-
-template <typename T, int N>
-__device__ __forceinline__ T transpose_sum(const T (&a)[N], int lane) {
-    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N = 1, 2, 4 or 8");
-    T v[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u) v[u] = a[u];
-    int off = 16;
-#pragma unroll
-    for (int m = N; m > 1; m >>= 1, off >>= 1) {
-        const bool hi = lane & off;
-#pragma unroll
-        for (int i = 0; i < m / 2; ++i) {
-            const T send = hi ? v[i] : v[i + m / 2];
-            const T keep = hi ? v[i + m / 2] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    T r = v[0];
-#pragma unroll
-    for (; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
-    return r;
-}
-
-template <int R>
-struct Pow2Rows {   // smallest of 1, 2, 4, 8 holding R rows
-    static constexpr int N = R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8;
-};
-
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
 template <typename T>
@@ -358,7 +314,7 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 const int q = base + u * kWarps;
                 const T r = bts[q] - sum;
                 const T w = w2s[q];
-                if (!(w < T(0))) {
+                if (!below_zero(w)) {
                     const T key = r * r * w;
                     if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
                 }
@@ -743,7 +699,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 if (transpose_rep<RPB>(lane) && q < nr) {
                     const T r = bts[q] - sum;
                     const T w = w2s[q];
-                    if (!(w < T(0))) {
+                    if (!below_zero(w)) {
                         const T key = r * r * w;
                         if (better(key, r0 + q, c.key, c.idx)) { c.key = key; c.alpha = r * w; c.idx = r0 + q; }
                     }
@@ -887,24 +843,17 @@ k_iterate_gram(IterProblem p, int R) {
             }
             ++round;
             __threadfence();
-            for (int c = tid; c < n; c += blockDim.x) xfull[c] = (double)__ldcg(xg + c);
+            for (int c = tid; c < n; c += blockDim.x) xfull[c] = widen(__ldcg(xg + c));
             __syncthreads();
-            // the first refresh widens this CTA's rows of At into At64 (exact),
-            // later ones read the FP64 copy: on this GPU the FP32 -> FP64
-            // conversions cost as much as the FP64 FMAs themselves
-            for (int q = warp; q < nr; q += kWarps) {
-                const float* a = At + (int64_t)(r0 + q) * p.ld;
-                double* a64 = p.At64 ? p.At64 + (int64_t)(r0 + q) * n : nullptr;
-                double acc = 0.0;
-                if (k == 0 || !a64) {
-                    acc = lane_dot_f64(a, xfull, n, lane);
-                    if (a64)
-                        for (int c = lane; c < n; c += 32) a64[c] = (double)a[c];
-                } else {
-                    acc = lane_dot_f64(a64, xfull, n, lane);
-                }
-                acc = warp_sum(acc);
-                if (lane == 0) rs[q] = (float)((double)bt[r0 + q] - acc);
+            // warp w sums the groups of kRefreshRows consecutive rows
+            // w, w + kWarps, ... (FP32 entries widened exactly, FP64 FMA)
+            for (int q0 = warp * kRefreshRows; q0 < nr; q0 += kWarps * kRefreshRows) {
+                const int m = min(kRefreshRows, nr - q0);
+                const double s = warp_rows_dot_f64<kRefreshRows>(At + (int64_t)(r0 + q0) * p.ld, p.ld, m,
+                                                                 xfull, n, lane);
+                const int u = transpose_row<kRefreshRows>(lane);
+                if (transpose_rep<kRefreshRows>(lane) && u < m)
+                    rs[q0 + u] = (float)(widen(bt[r0 + q0 + u]) - s);
             }
             __syncthreads();
         }
@@ -955,7 +904,8 @@ k_iterate_gram(IterProblem p, int R) {
 }
 
 // --------------------------------------------------------- final check
-constexpr int kFinalThreads = 256;
+constexpr int kFinalThreads = 128;
+constexpr int kFinalRows = 8;      // rows a warp sums at once in the final check
 
 __device__ __forceinline__ double block_sum_f64(double v, double* sh) {
     v = warp_sum(v);
@@ -975,13 +925,18 @@ k_final_rows(const T* __restrict__ At, int64_t ld, int d, int n, const T* __rest
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     double rr = 0.0, bb = 0.0, empty = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < d; j += nwarps) {
-        double s = lane_dot_f64(At + j * ld, x, n, lane);
-        s = warp_sum(s);
-        if (lane == 0) {
-            const double r = (double)bt[j] - s;
+    // a warp takes kFinalRows consecutive rows at a time
+    for (int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kFinalRows; j0 < d;
+         j0 += nwarps * kFinalRows) {
+        const int nr = (int)(d - j0 < kFinalRows ? d - j0 : kFinalRows);
+        const double s = warp_rows_dot_f64<kFinalRows>(At + j0 * ld, ld, nr, x, n, lane);
+        const int u = transpose_row<kFinalRows>(lane);
+        if (transpose_rep<kFinalRows>(lane) && u < nr) {
+            const int64_t j = j0 + u;
+            const double bj = widen(bt[j]);
+            const double r = bj - s;
             rr += r * r;
-            bb += (double)bt[j] * (double)bt[j];
+            bb += bj * bj;
             empty += (N2[j] > 0.0) ? 0.0 : 1.0;
         }
     }
@@ -1027,7 +982,8 @@ k_final_reduce(const double* __restrict__ part, int nparts, const T* __restrict_
 int final_blocks(int d) {
     DevInfo di;
     dev_info(&di);
-    int64_t blocks = ((int64_t)d + 7) / 8;
+    const int64_t rows_per_block = (int64_t)kFinalRows * (kFinalThreads / 32);
+    int64_t blocks = ((int64_t)d + rows_per_block - 1) / rows_per_block;
     const int64_t cap = (int64_t)(di.sms > 0 ? di.sms : 1) * 4;
     return (int)(blocks < cap ? blocks : cap);
 }

@@ -85,7 +85,6 @@ struct IterProblem {
     Slot* slots;               // 2 * grid
     void* xg;                  // n elements (GRAM path refresh)
     const float* G;  int64_t ldg;  // GRAM path
-    double* At64;              // GRAM path: d x n FP64 copy of At for the refresh (nullable)
     int refresh_every;
     int32_t* ik_log;  int64_t ik_log_len;
     void* x_log;  int64_t x_log_len;

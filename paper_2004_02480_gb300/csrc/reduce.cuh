@@ -20,6 +20,33 @@ __device__ __forceinline__ bool better(T ka, int32_t ia, T kb, int32_t ib) {
     return ka > kb || (ka == kb && ia < ib);
 }
 
+// Monotone 64-bit code of an FP64 key, in the order of better(): NaN
+// highest, a negative key ("no candidate") lowest, otherwise the bit pattern
+// + 1 (non-negative doubles order as their bits).  Integer operations only:
+// this GPU runs FP64 -- compares included -- at 1/64 of the FP32 rate.
+__device__ __forceinline__ uint64_t key_code(double k) {
+    const uint64_t u = (uint64_t)__double_as_longlong(k);
+    const uint64_t a = u & 0x7FFFFFFFFFFFFFFFull;
+    return a > 0x7FF0000000000000ull ? ~0ull : ((u >> 63) ? 0ull : u + 1ull);
+}
+
+// The same order for FP64 keys through their codes.  Keys are r^2 w >= +0,
+// NaN, or the negative "no candidate" marker, on which both orders agree.
+template <>
+__device__ __forceinline__ bool better<double>(double ka, int32_t ia, double kb, int32_t ib) {
+    const uint64_t a = key_code(ka), b = key_code(kb);
+    return a > b || (a == b && ia < ib);
+}
+
+// w < 0 for a row weight (1/||At_j||^2, -1 for a zero row, NaN for a bad
+// row); the FP64 form tests the bits (negative and not NaN).
+__device__ __forceinline__ bool below_zero(float w) { return w < 0.0f; }
+__device__ __forceinline__ bool below_zero(double w) {
+    const uint64_t u = (uint64_t)__double_as_longlong(w);
+    const uint64_t a = u & 0x7FFFFFFFFFFFFFFFull;
+    return (u >> 63) && a != 0ull && a <= 0x7FF0000000000000ull;
+}
+
 template <typename T>
 struct Red {
     T key, alpha, stat;
@@ -62,8 +89,7 @@ __device__ __forceinline__ void warp_reduce(Red<float>& c) {
 // at 1/64 of the FP32 rate.  Same ordering as better(); the statistic is
 // summed with the same shuffle tree as before.
 __device__ __forceinline__ void warp_reduce(Red<double>& c) {
-    uint64_t code = c.key != c.key ? ~0ull
-                                   : (c.key < 0.0 ? 0ull : (uint64_t)__double_as_longlong(c.key) + 1ull);
+    uint64_t code = key_code(c.key);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const uint64_t c2 = __shfl_xor_sync(0xffffffffu, code, o);
@@ -75,6 +101,53 @@ __device__ __forceinline__ void warp_reduce(Red<double>& c) {
     c.key = code == ~0ull ? (double)NAN
           : code == 0ull ? -1.0 : __longlong_as_double((long long)(code - 1ull));
 }
+
+// --------------------------------------------------- row sums of a warp
+// Sums of a warp's N rows (N = 1, 2, 4, 8; a[u] = this lane's partial of row
+// u) by a transposed butterfly: each of the first log2(N) levels halves the
+// rows a lane carries, so the N sums cost 5 + N - 1 shuffles and adds instead
+// of 5 N, and lane l ends with the sum of row transpose_row<N>(l) (lane bits
+// 4, 3, 2 from the top).  Every level adds the same pairs as the xor
+// butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
+// warp_sum of its row.
+template <int N>
+__device__ __forceinline__ int transpose_row(int lane) {
+    return N == 8 ? ((lane >> 2) & 7) : N == 4 ? ((lane >> 3) & 3) : N == 2 ? ((lane >> 4) & 1) : 0;
+}
+
+// The lane of each group holding one row that reports it (lowest free bits 0).
+template <int N>
+__device__ __forceinline__ bool transpose_rep(int lane) {
+    return (lane & (32 / N - 1)) == 0;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ T transpose_sum(const T (&a)[N], int lane) {
+    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N = 1, 2, 4 or 8");
+    T v[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) v[u] = a[u];
+    int off = 16;
+#pragma unroll
+    for (int m = N; m > 1; m >>= 1, off >>= 1) {
+        const bool hi = lane & off;
+#pragma unroll
+        for (int i = 0; i < m / 2; ++i) {
+            const T send = hi ? v[i] : v[i + m / 2];
+            const T keep = hi ? v[i + m / 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    T r = v[0];
+#pragma unroll
+    for (; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+    return r;
+}
+
+template <int R>
+struct Pow2Rows {   // smallest of 1, 2, 4, 8 holding R rows
+    static constexpr int N = R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8;
+};
 
 // CTA-wide reduction with a single barrier: warps post their partial results
 // in one of two shared buffers (alternating between calls), then every warp

@@ -16,6 +16,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "fp64.cuh"
 #include "kernels.h"
 
 namespace csk {
@@ -339,26 +340,21 @@ k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __rest
 }
 
 // ----------------------------------------------------------- row norms
+// A warp takes kNormRows consecutive rows at a time; per row the squares of
+// columns lane, lane + 32, ... accumulate in order (FMA), then a butterfly.
+constexpr int kNormRows = 8;
+
 template <typename T>
 __global__ void k_row_norms(const T* __restrict__ A, int64_t ld, int rows, int n,
                             double* __restrict__ N2) {
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < rows;
-         j += nwarps) {
-        // columns lane, lane + 32, ... in order, eight loads in flight
-        const T* a = A + j * ld;
-        const int lane = lane_id();
-        double s = 0.0;
-        for (int c0 = lane; c0 < n; c0 += 32 * 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = c0 + 32 * u < n ? (double)a[c0 + 32 * u] : 0.0;
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + 32 * u < n) s += v[u] * v[u];
-        }
-        s = warp_sum(s);
-        if (lane == 0) N2[j] = s;
+    const int lane = lane_id();
+    for (int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kNormRows;
+         j0 < rows; j0 += nwarps * kNormRows) {
+        const int nr = (int)(rows - j0 < kNormRows ? rows - j0 : kNormRows);
+        const double s = warp_rows_sq_f64<kNormRows>(A + j0 * ld, ld, nr, n, lane);
+        const int u = transpose_row<kNormRows>(lane);
+        if (transpose_rep<kNormRows>(lane) && u < nr) N2[j0 + u] = s;
     }
 }
 
@@ -464,7 +460,7 @@ cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int
                              cudaStream_t st) {
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
-    int64_t blocks = ((int64_t)rows + 7) / 8;
+    int64_t blocks = ((int64_t)rows + 8 * kNormRows - 1) / (8 * kNormRows);   // 8 warps per block
     if (blocks > (int64_t)di.sms * 32) blocks = (int64_t)di.sms * 32;
     if (dtype == CSK_F32)
         k_row_norms<float><<<(int)blocks, 256, 0, st>>>((const float*)A, ld, rows, n, N2);

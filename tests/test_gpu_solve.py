@@ -362,3 +362,33 @@ def test_stream_variant_fp64_sketched_matches_shared_memory_variant(csk):
         _compare_prefix(ik[:info["iters"]], ref, 1e-9)
         out.append(x)
     assert np.sum((out[0] - out[1]) ** 2) / np.sum(s.x_star ** 2) <= 1e-20
+
+
+def test_fp64_check_widens_subnormals_exactly(csk):
+    """The FP64 row norms and final check widen FP32 entries to binary64 with
+    integer operations; the widening must be exact for subnormal floats and
+    signed zeros too.  Unsketched solve (d = 0) stopped before its first step
+    (max_iter = 0), so x = x0 and the check reports ||b - A x0|| / ||b||:
+    column 0 of A holds signed subnormals k 2^-149, column 1 signed zeros, b
+    the smallest normals, x0 = (1, 0.5, 0, 0).  Every product and difference
+    is exact in binary64, so the expected value is fixed up to the order of
+    the final sums; a subnormal flushed to zero or given a wrong exponent
+    moves it by far more than the tolerance, and a flushed row norm would
+    count the row as empty."""
+    rng = np.random.default_rng(3)
+    m, n = 256, 4
+    a0 = rng.integers(1, 2 ** 23, size=m) * 2.0 ** -149 * rng.choice([-1.0, 1.0], size=m)
+    A = np.zeros((m, n), np.float32)
+    A[:, 0] = a0.astype(np.float32)
+    A[:, 1] = np.where(rng.random(m) < 0.5, np.float32(-0.0), np.float32(0.0))
+    assert np.array_equal(A[:, 0].astype(np.float64), a0)          # representable exactly
+    b = (rng.integers(2 ** 23, 2 ** 24, size=m) * 2.0 ** -149).astype(np.float32)
+    x0 = np.array([1.0, 0.5, 0.0, 0.0], np.float32)
+    p = csk.csk_params_default(d=0, tol=1e-6, max_iter=0)
+    x, info = csk.csk_solve(_to(A), _to(b), p, x0=_to(x0))
+    assert info["iters"] == 0
+    assert np.array_equal(x.cpu().numpy(), x0)
+    r = b.astype(np.float64) - A.astype(np.float64) @ x0.astype(np.float64)
+    want = np.sqrt(np.sum(r * r) / np.sum(b.astype(np.float64) ** 2))
+    assert abs(info["resid"] - want) <= 1e-13 * want
+    assert info["empty_rows"] == 0
