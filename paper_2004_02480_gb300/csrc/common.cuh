@@ -36,6 +36,18 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialization attribute may be scheduled while its predecessor in
+// the stream still runs: pdl_wait() returns once that predecessor has
+// completed and its writes are visible (so every read of its output, and
+// every write, comes after it); pdl_trigger() lets this kernel's own
+// successor be scheduled.  Both do nothing in a kernel launched without the
+// attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;

@@ -28,8 +28,9 @@ cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_
 void note_launches(int k);
 
 // ------------------------------------------------------------- sketch
-// Scratch of the counting sort: cnt[d], off[d+1], perm_tmp[m], perm[m],
-// scan partials.  All int32.
+// Scratch of the counting sort: cnt[d + 1] (bucket counts, then the bucket
+// claim counter of the segmented sum), off[d+1], perm_tmp[m], perm[m], scan
+// partials.  All int32.
 struct SortScratch {
     int32_t* cnt;
     int32_t* off;

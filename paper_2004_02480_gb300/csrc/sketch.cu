@@ -19,6 +19,10 @@
 #include "fp64.cuh"
 #include "kernels.h"
 
+#ifndef CSK_SKETCH_PDL
+#define CSK_SKETCH_PDL 1
+#endif
+
 namespace csk {
 
 namespace {
@@ -26,12 +30,39 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 4096 buckets per tile
+constexpr int kScanSingleItems = 32;
+constexpr int kScanSingle = kScanThreads * kScanSingleItems;   // one-block scan up to 32768 buckets
 constexpr int kSortCap = 1024;           // rows of a bucket ordered in shared memory
 
 inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// before its predecessor in the stream has finished, and waits for it inside
+// (pdl_wait), which hides the launch gap between the short kernels of the
+// sketch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = CSK_SKETCH_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------- histogram
-__global__ void k_hist(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict__ cnt) {
+// Bucket counts, and each row's slot among the rows of its bucket (in the
+// order the atomics happen to run; the segmented sum orders every bucket by
+// row index afterwards).  Lanes of a warp that share a bucket take
+// consecutive slots from one atomic.
+__global__ void k_hist(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict__ cnt,
+                       int32_t* __restrict__ slot) {
+    pdl_trigger();
     // warp-uniform trip count: every lane reaches the match below together
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = lane_id();
@@ -41,24 +72,29 @@ __global__ void k_hist(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict
         const bool valid = i < m;
         const int32_t j = valid ? row_bucket(row_hash(seed, (uint64_t)i), d) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, j);
-        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[j], __popc(peers));
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (valid && lane == leader) first = atomicAdd(&cnt[j], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (valid) slot[i] = first + __popc(peers & lanemask_lt());
     }
 }
 
 // ------------------------------------------------------------------ scan
-// Block-wide exclusive scan of kScanTile int32 values starting at `first`.
+// Block-wide exclusive scan of kScanThreads * ITEMS int32 values starting at
+// `first` (thread t takes ITEMS consecutive values).
+template <int ITEMS>
 __device__ __forceinline__ int block_scan_tile(const int32_t* __restrict__ cnt, int64_t first,
                                                int64_t d, int carry_in, int32_t* __restrict__ out,
                                                int* sh_warp) {
     const int t = threadIdx.x;
-    const int64_t i0 = first + (int64_t)t * kScanItems;
-    int v[kScanItems];
+    const int64_t i0 = first + (int64_t)t * ITEMS;
+    int v[ITEMS];
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) v[q] = (i0 + q < d) ? cnt[i0 + q] : 0;
-    int incl[kScanItems];
+    for (int q = 0; q < ITEMS; ++q) v[q] = (i0 + q < d) ? cnt[i0 + q] : 0;
     int run = 0;
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) { run += v[q]; incl[q] = run; }
+    for (int q = 0; q < ITEMS; ++q) run += v[q];
     // warp inclusive scan of the per-thread totals
     int w = run;
 #pragma unroll
@@ -81,9 +117,12 @@ __device__ __forceinline__ int block_scan_tile(const int32_t* __restrict__ cnt, 
     __syncthreads();
     const int warp_excl = warp ? sh_warp[warp - 1] : 0;
     const int base = carry_in + warp_excl + (w - run);
+    int ex = base;
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q)
-        if (i0 + q < d) out[i0 + q] = base + incl[q] - v[q];
+    for (int q = 0; q < ITEMS; ++q) {
+        if (i0 + q < d) out[i0 + q] = ex;
+        ex += v[q];
+    }
     const int total = sh_warp[kScanThreads / 32 - 1];
     __syncthreads();
     return total;
@@ -91,6 +130,8 @@ __device__ __forceinline__ int block_scan_tile(const int32_t* __restrict__ cnt, 
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_partials(const int32_t* __restrict__ cnt, int64_t d, int32_t* __restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int sh[32];
     const int64_t i0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     int s = 0;
@@ -109,6 +150,8 @@ k_scan_partials(const int32_t* __restrict__ cnt, int64_t d, int32_t* __restrict_
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_tiles(const int32_t* __restrict__ cnt, int64_t d, const int32_t* __restrict__ part,
              int32_t* __restrict__ off) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int sh[32];
     __shared__ int carry;
     // carry-in of this tile: sum of the partials of the tiles before it
@@ -125,29 +168,31 @@ k_scan_tiles(const int32_t* __restrict__ cnt, int64_t d, const int32_t* __restri
     __syncthreads();
     const int c = carry;
     __syncthreads();
-    const int total = block_scan_tile(cnt, (int64_t)blockIdx.x * kScanTile, d, c, off, sh);
+    const int total = block_scan_tile<kScanItems>(cnt, (int64_t)blockIdx.x * kScanTile, d, c, off, sh);
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) off[d] = c + total;
 }
 
+// The whole scan in one block, for d <= kScanSingle.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_single(const int32_t* __restrict__ cnt, int64_t d, int32_t* __restrict__ off) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ int sh[32];
+    const int total = block_scan_tile<kScanSingleItems>(cnt, 0, d, 0, off, sh);
+    if (threadIdx.x == 0) off[d] = total;
+}
+
 // --------------------------------------------------------------- scatter
-__global__ void k_scatter(int64_t m, uint32_t d, uint64_t seed, int32_t* __restrict__ cnt,
+// Row i goes to perm_tmp[off[h(i)] + slot[i]]: no atomics, the slots were
+// taken by the histogram pass.
+__global__ void k_scatter(int64_t m, uint32_t d, uint64_t seed, const int32_t* __restrict__ slot,
                           const int32_t* __restrict__ off, int32_t* __restrict__ perm_tmp) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = lane_id();
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m;
-         base += stride) {
-        const int64_t i = base + lane;
-        const bool valid = i < m;
-        const int32_t j = valid ? row_bucket(row_hash(seed, (uint64_t)i), d) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, j);
-        const int leader = __ffs(peers) - 1;
-        const int np = __popc(peers);
-        const int rk = __popc(peers & lanemask_lt());
-        int top = 0;
-        if (valid && lane == leader) top = atomicSub(&cnt[j], np);
-        top = __shfl_sync(0xffffffffu, top, leader);
-        // this group owns bucket-relative slots [top - np, top)
-        if (valid) perm_tmp[off[j] + top - np + rk] = (int32_t)i;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int32_t j = row_bucket(row_hash(seed, (uint64_t)i), d);
+        perm_tmp[off[j] + slot[i]] = (int32_t)i;
     }
 }
 
@@ -239,7 +284,7 @@ __device__ __forceinline__ double seg_chunk(const T* __restrict__ src, int64_t l
     return sq;
 }
 
-// One CTA per bucket (grid-stride).  The bucket's rows, grouped but in no
+// Resident CTAs claim buckets one at a time from a counter.  The bucket's rows, grouped but in no
 // particular order by the scatter, are ranked by row index in shared memory
 // (rows are distinct, so every rank is unique) and written to perm in
 // ascending order; a bucket larger than kSortCap is regenerated in ascending
@@ -248,18 +293,27 @@ __device__ __forceinline__ double seg_chunk(const T* __restrict__ src, int64_t l
 // the bucket's rows in that order; the FP64 row norm is combined across
 // warps in a fixed order.
 template <typename T, int V, int CPL, int U>
-__global__ void __launch_bounds__(128)
+// 10 CTAs per SM in FP32 (48 registers; at 56 the kernel ran markedly slower), 7 in FP64
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 10 : 7)
 k_segsum(const T* __restrict__ A, int64_t lda, int n, int64_t m,
          const int32_t* __restrict__ perm_tmp, int32_t* __restrict__ perm,
          const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ At,
-         double* __restrict__ N2) {
+         double* __restrict__ N2, int32_t* __restrict__ next) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double part[4];
     __shared__ __align__(16) int32_t ubuf[kSortCap];
     __shared__ __align__(16) int32_t sbuf[kSortCap];
     constexpr int CW = 32 * V * CPL;                 // columns per chunk
     const int tid = threadIdx.x, nt = blockDim.x;
     const int W = nt >> 5, warp = tid >> 5, lane = lane_id();
-    for (int64_t j = blockIdx.x; j < d; j += gridDim.x) {
+    __shared__ int32_t claim;
+    for (;;) {
+        // the next unclaimed bucket: every CTA stays busy until the last ones
+        if (tid == 0) claim = atomicAdd(next, 1);
+        __syncthreads();
+        const int64_t j = claim;
+        if (j >= d) break;
         const int32_t p0 = off[j], p1 = off[j + 1], cnt = p1 - p0;
         const int32_t* rows = sbuf;
         int32_t q0 = 0;
@@ -317,6 +371,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __restrict__ perm,
            const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ Bt) {
+    pdl_wait();
     const int lane = lane_id();
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < d; j += nwarps) {
@@ -381,14 +436,14 @@ __global__ void __launch_bounds__(1024) k_norm2(const T* __restrict__ v, int64_t
 // ------------------------------------------------------------ host side
 size_t sort_scratch_bytes(int64_t m, int64_t d) {
     const int64_t tiles = (d + kScanTile - 1) / kScanTile;
-    return (size_t)(align_up(4 * d, 256) + align_up(4 * (d + 1), 256) + 2 * align_up(4 * m, 256) +
+    return (size_t)(align_up(4 * (d + 1), 256) + align_up(4 * (d + 1), 256) + 2 * align_up(4 * m, 256) +
                     align_up(4 * tiles, 256));
 }
 
 void carve_sort_scratch(void* base, int64_t m, int64_t d, SortScratch* s) {
     char* p = static_cast<char*>(base);
     const int64_t tiles = (d + kScanTile - 1) / kScanTile;
-    s->cnt = reinterpret_cast<int32_t*>(p);       p += align_up(4 * d, 256);
+    s->cnt = reinterpret_cast<int32_t*>(p);       p += align_up(4 * (d + 1), 256);
     s->off = reinterpret_cast<int32_t*>(p);       p += align_up(4 * (d + 1), 256);
     s->perm_tmp = reinterpret_cast<int32_t*>(p);  p += align_up(4 * m, 256);
     s->perm = reinterpret_cast<int32_t*>(p);      p += align_up(4 * m, 256);
@@ -400,18 +455,28 @@ cudaError_t launch_bucket_group(int64_t m, int64_t d, uint64_t seed, const SortS
                                 cudaStream_t st) {
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
-    cudaError_t e = cudaMemsetAsync(s.cnt, 0, (size_t)d * 4, st);
+    cudaError_t e = cudaMemsetAsync(s.cnt, 0, (size_t)(d + 1) * 4, st);   // counts and the claim counter
     if (e != cudaSuccess) return e;
     const int threads = 256;
     int64_t blocks = (m + threads - 1) / threads;
     if (blocks > (int64_t)di.sms * 16) blocks = (int64_t)di.sms * 16;
-    k_hist<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt);
-    const int64_t tiles = (d + kScanTile - 1) / kScanTile;
-    if (tiles > 1) k_scan_partials<<<(int)tiles, kScanThreads, 0, st>>>(s.cnt, d, s.part);
-    k_scan_tiles<<<(int)tiles, kScanThreads, 0, st>>>(s.cnt, d, s.part, s.off);
-    k_scatter<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt, s.off, s.perm_tmp);
-    note_launches(tiles > 1 ? 4 : 3);
-    return cudaGetLastError();
+    // the slots live in perm until the segmented sum writes the sorted rows there
+    k_hist<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt, s.perm);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (d <= kScanSingle) {
+        e = launch_dep(k_scan_single, 1, kScanThreads, st, s.cnt, d, s.off);
+        note_launches(3);
+    } else {
+        const int64_t tiles = (d + kScanTile - 1) / kScanTile;
+        e = launch_dep(k_scan_partials, (int)tiles, kScanThreads, st, s.cnt, d, s.part);
+        if (e == cudaSuccess)
+            e = launch_dep(k_scan_tiles, (int)tiles, kScanThreads, st, s.cnt, d, s.part, s.off);
+        note_launches(4);
+    }
+    if (e == cudaSuccess)
+        e = launch_dep(k_scatter, (int)blocks, threads, st, m, (uint32_t)d, seed, s.perm, s.off,
+                       s.perm_tmp);
+    return e;
 }
 
 cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
@@ -419,41 +484,49 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
                           void* At, void* Bt, double* N2, cudaStream_t st) {
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
-    int64_t blocks = d;
-    if (blocks > (int64_t)di.sms * 64) blocks = (int64_t)di.sms * 64;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
     // warps per bucket: one per column chunk, at most 4
     auto warps_for = [&](int cw) { int w = (n + cw - 1) / cw; return w < 1 ? 1 : (w > 4 ? 4 : w); };
+    const int bs = 32 * warps_for(128);
+    // as many CTAs as stay resident (they claim the buckets), at most d
+    auto grid_for = [&](const void* fn, int* g) -> cudaError_t {
+        int per_sm = 0;
+        const cudaError_t ce = cached_occupancy(fn, bs, 0, &per_sm);
+        if (ce != cudaSuccess) return ce;
+        const int64_t r = (int64_t)(per_sm > 0 ? per_sm : 1) * di.sms;
+        *g = (int)(r < d ? r : d);
+        return cudaSuccess;
+    };
+    cudaError_t e;
+    int blocks = 0;
     if (dtype == CSK_F32) {
         const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
-        if (vec)
-            k_segsum<float, 4, 1, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2);
-        else
-            k_segsum<float, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At, N2);
+        const auto fn = vec ? k_segsum<float, 4, 1, 4> : k_segsum<float, 1, 4, 4>;
+        e = grid_for((const void*)fn, &blocks);
+        if (e == cudaSuccess)
+            e = launch_dep(fn, blocks, bs, st, (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off,
+                           d, seed, (float*)At, N2, s.cnt + d);
     } else {
         const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
-        if (vec)
-            k_segsum<double, 2, 2, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2);
-        else
-            k_segsum<double, 1, 4, 4><<<(int)blocks, 32 * warps_for(128), 0, st>>>(
-                (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (double*)At, N2);
+        const auto fn = vec ? k_segsum<double, 2, 2, 4> : k_segsum<double, 1, 4, 4>;
+        e = grid_for((const void*)fn, &blocks);
+        if (e == cudaSuccess)
+            e = launch_dep(fn, blocks, bs, st, (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off,
+                           d, seed, (double*)At, N2, s.cnt + d);
     }
     note_launches(1);
-    if (B && nrhs > 0) {
+    if (e == cudaSuccess && B && nrhs > 0) {
         int64_t bblocks = ((int64_t)d + 7) / 8;
         if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
         if (dtype == CSK_F32)
-            k_segsum_b<float><<<(int)bblocks, 256, 0, st>>>((const float*)B, ldb, nrhs, s.perm, s.off,
-                                                            d, seed, (float*)Bt);
+            e = launch_dep(k_segsum_b<float>, (int)bblocks, 256, st, (const float*)B, ldb, nrhs,
+                           s.perm, s.off, d, seed, (float*)Bt);
         else
-            k_segsum_b<double><<<(int)bblocks, 256, 0, st>>>((const double*)B, ldb, nrhs, s.perm,
-                                                             s.off, d, seed, (double*)Bt);
+            e = launch_dep(k_segsum_b<double>, (int)bblocks, 256, st, (const double*)B, ldb, nrhs,
+                           s.perm, s.off, d, seed, (double*)Bt);
         note_launches(1);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int n, double* N2,

@@ -36,7 +36,9 @@ def _gpu_sketch(csk, A, b, d, seed):
 
 
 @pytest.mark.parametrize("m,d", [(1, 1), (7, 3), (2000, 500), (2000, 2000), (2000, 5000),
-                                 (100000, 1), (1_000_000, 500), (1_000_000, 20000), (33, 1000)])
+                                 (100000, 1), (1_000_000, 500), (1_000_000, 20000), (33, 1000),
+                                 # one-block scan up to 32768 buckets, tiled scan above
+                                 (100000, 32768), (100000, 32769), (300000, 100000)])
 def test_sort_bit_exact(csk, m, d):
     seed = 17 + m + d
     A = np.zeros((m, 4), np.float32)
