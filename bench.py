@@ -114,7 +114,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-LOOP_SOURCES = ("iterate.cu", "common.cuh", "reduce.cuh", "async.cuh")
+LOOP_SOURCES = ("iterate.cu", "common.cuh", "reduce.cuh", "async.cuh", "fp64.cuh")
 
 
 def _source_hash(*files):

@@ -30,8 +30,7 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 4096 buckets per tile
-constexpr int kScanSingleItems = 32;
-constexpr int kScanSingle = kScanThreads * kScanSingleItems;   // one-block scan up to 32768 buckets
+constexpr int kScanSingle = kScanThreads * 32;   // one-block scan up to 32768 buckets (R <= 8)
 constexpr int kSortCap = 1024;           // rows of a bucket ordered in shared memory
 
 inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -172,14 +171,77 @@ k_scan_tiles(const int32_t* __restrict__ cnt, int64_t d, const int32_t* __restri
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) off[d] = c + total;
 }
 
-// The whole scan in one block, for d <= kScanSingle.
+// The whole scan in one block of kScanThreads, for d <= kScanSingle.  Warp w
+// owns the contiguous segment [128 R w, 128 R (w + 1)) and reads it in R
+// coalesced rounds of 128 counts (4 per lane); each round is scanned across
+// the warp with shuffles and carried into the next, then the warps' totals
+// are scanned in shared memory.
+template <int R>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_single(const int32_t* __restrict__ cnt, int64_t d, int32_t* __restrict__ off) {
     pdl_wait();
     pdl_trigger();
-    __shared__ int sh[32];
-    const int total = block_scan_tile<kScanSingleItems>(cnt, 0, d, 0, off, sh);
-    if (threadIdx.x == 0) off[d] = total;
+    __shared__ int wsum[kScanThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int64_t seg = (int64_t)warp * 128 * R;
+    int v[R][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = seg + 128 * r + 4 * lane;
+        if (i + 3 < d) {
+            const int4 t = *reinterpret_cast<const int4*>(cnt + i);
+            v[r][0] = t.x; v[r][1] = t.y; v[r][2] = t.z; v[r][3] = t.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[r][q] = i + q < d ? cnt[i + q] : 0;
+        }
+    }
+    int excl[R];
+    int carry = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = v[r][0] + v[r][1] + v[r][2] + v[r][3];
+        int sc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += y;
+        }
+        excl[r] = carry + sc - t;
+        carry += __shfl_sync(0xffffffffu, sc, 31);
+    }
+    if (lane == 0) wsum[warp] = carry;
+    __syncthreads();
+    if (warp == 0) {
+        const int t = wsum[lane];
+        int sc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += y;
+        }
+        wsum[lane] = sc - t;                       // exclusive offset of warp `lane`
+        if (lane == 31) off[d] = sc;               // total
+    }
+    __syncthreads();
+    const int base = wsum[warp];
+    const bool vec_out = (reinterpret_cast<uintptr_t>(off) & 15) == 0;   // off may be the caller's
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = seg + 128 * r + 4 * lane;
+        int e[4];
+        e[0] = base + excl[r];
+        e[1] = e[0] + v[r][0];
+        e[2] = e[1] + v[r][1];
+        e[3] = e[2] + v[r][2];
+        if (vec_out && i + 3 < d) {
+            *reinterpret_cast<int4*>(off + i) = make_int4(e[0], e[1], e[2], e[3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i + q < d) off[i + q] = e[q];
+        }
+    }
 }
 
 // --------------------------------------------------------------- scatter
@@ -464,7 +526,11 @@ cudaError_t launch_bucket_group(int64_t m, int64_t d, uint64_t seed, const SortS
     k_hist<<<(int)blocks, threads, 0, st>>>(m, (uint32_t)d, seed, s.cnt, s.perm);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d <= kScanSingle) {
-        e = launch_dep(k_scan_single, 1, kScanThreads, st, s.cnt, d, s.off);
+        // rounds of 128 counts per warp: 32 warps x 128 R >= d
+        const int64_t need = (d + 32 * 128 - 1) / (32 * 128);
+        auto fn = need <= 1 ? k_scan_single<1> : need <= 2 ? k_scan_single<2>
+                : need <= 4 ? k_scan_single<4> : k_scan_single<8>;
+        e = launch_dep(fn, 1, kScanThreads, st, s.cnt, d, s.off);
         note_launches(3);
     } else {
         const int64_t tiles = (d + kScanTile - 1) / kScanTile;

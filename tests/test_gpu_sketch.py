@@ -49,6 +49,30 @@ def test_sort_bit_exact(csk, m, d):
     assert np.array_equal(s.perm.cpu().numpy(), perm)
 
 
+@pytest.mark.parametrize("d", [3000, 40000])
+def test_sort_offsets_into_unaligned_buffer(csk, d):
+    """off_out and perm_out may be any int32-aligned caller buffers (here 4
+    bytes past a 16-byte boundary): the scans and the scatter must not assume
+    vector alignment there."""
+    m, n, seed = 50000, 4, 5
+    A = torch.zeros((m, n), dtype=torch.float32, device=DEV)
+    At = torch.empty((d, n), dtype=torch.float32, device=DEV)
+    obuf = torch.zeros(d + 2, dtype=torch.int32, device=DEV)
+    pbuf = torch.zeros(m + 1, dtype=torch.int32, device=DEV)
+    off_view, perm_view = obuf[1:], pbuf[1:]
+    assert off_view.data_ptr() % 16 == 4 and perm_view.data_ptr() % 16 == 4
+    ws = csk._workspace(csk.csk_sketch_workspace_size(m, d), A.device)
+    rc = csk.lib().csk_sketch(csk._ptr(A), m, n, n, None, 0, 0, csk.CSK_F32, d, seed, csk._ptr(At),
+                              None, None, csk._ptr(perm_view), csk._ptr(off_view), csk._ptr(ws),
+                              ws.numel(), csk._stream(A.device))
+    assert rc == 0
+    torch.cuda.synchronize()
+    h, _ = oracle.count_sketch_map(seed, m, d)
+    _, off, perm = oracle.stable_count_sort(h, d)
+    assert np.array_equal(off_view.cpu().numpy(), off)
+    assert np.array_equal(perm_view.cpu().numpy(), perm)
+
+
 @pytest.mark.parametrize("m,n,d,R", [(1, 1, 1, 1), (7, 3, 3, 1), (2000, 50, 500, 1),
                                      (5000, 64, 300, 3), (3000, 257, 1000, 1), (1000, 33, 2000, 2),
                                      (20000, 1000, 700, 0), (40000, 12, 10, 64)])
