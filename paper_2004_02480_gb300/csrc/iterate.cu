@@ -42,7 +42,7 @@ namespace {
 constexpr int kIterThreads = 256;
 constexpr int kWarps = kIterThreads / 32;
 constexpr int64_t kDefaultSpin = 1ll << 22;
-constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass (ILP; 1, 2, 4 or 8)
+constexpr int kRowsPerWarp = 8;          // rows a warp scores in one pass at most (1, 2, 4 or 8)
 constexpr int kRefreshRows = 4;          // rows a warp sums at once in the FP64 refresh
 
 // ---------------------------------------------------------- exchanges
@@ -177,6 +177,26 @@ __device__ __forceinline__ int decide(T stat, T threshold, int64_t k, int64_t ma
     return INT_MIN;
 }
 
+// FP64: the same tests on the integer pipe.  stat is a sum of squares and
+// threshold = tol * ||.||^2 with tol >= 0, so both are +0, positive, Inf or
+// NaN, and for those "stat <= threshold" is an unsigned comparison of the bit
+// patterns unless one of them is NaN.  The key tests read its code.
+template <>
+__device__ __forceinline__ int decide<double>(double stat, double threshold, int64_t k,
+                                              int64_t max_iter, double key) {
+    const uint64_t sb = (uint64_t)__double_as_longlong(stat);
+    const uint64_t tb = (uint64_t)__double_as_longlong(threshold);
+    const uint64_t kInf = 0x7FF0000000000000ull;
+    if ((sb & ~(1ull << 63)) <= kInf && (tb & ~(1ull << 63)) <= kInf &&
+        ((sb << 1) == 0 || sb <= tb))
+        return CSK_OK;
+    if (k >= max_iter) return CSK_MAXITER;
+    const uint64_t kc = key_code(key);
+    if (kc == ~0ull || kc == 0ull) return CSK_ENUMERIC;     // NaN, or no non-zero row
+    if (kc == 1ull) return CSK_OK;                           // every residual is exactly 0
+    return INT_MIN;
+}
+
 __device__ __forceinline__ void finish(csk_info* info, int status, int64_t k) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         info->iters = k;
@@ -228,7 +248,7 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
 
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
-template <typename T>
+template <typename T, int NR>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -275,21 +295,21 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     int status = CSK_OK;
     for (;;) {
         // Phase A: residuals of the owned rows.  Warp w scores rows
-        // w, w + kWarps, ... (round robin), up to kRowsPerWarp in one pass
+        // w, w + kWarps, ... (round robin), up to NR in one pass
         // over the columns so their loads overlap.
         Red<T> c;
         c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
-        for (int base = warp; base < nr; base += kWarps * kRowsPerWarp) {
-            const int myrows = min(kRowsPerWarp, (nr - base + kWarps - 1) / kWarps);
-            T acc[kRowsPerWarp];
+        for (int base = warp; base < nr; base += kWarps * NR) {
+            const int myrows = min(NR, (nr - base + kWarps - 1) / kWarps);
+            T acc[NR];
 #pragma unroll
-            for (int u = 0; u < kRowsPerWarp; ++u) acc[u] = T(0);
+            for (int u = 0; u < NR; ++u) acc[u] = T(0);
             if (vec4) {
                 const float4* x4 = reinterpret_cast<const float4*>(xs);
                 for (int c4 = lane; c4 < (n >> 2); c4 += 32) {
                     const float4 xv = x4[c4];
 #pragma unroll
-                    for (int u = 0; u < kRowsPerWarp; ++u)
+                    for (int u = 0; u < NR; ++u)
                         if (u < myrows) {
                             const float4 a = reinterpret_cast<const float4*>(
                                 Abase + (int64_t)(base + u * kWarps) * lda)[c4];
@@ -303,14 +323,14 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 for (int col = lane; col < n; col += 32) {
                     const T xv = xs[col];
 #pragma unroll
-                    for (int u = 0; u < kRowsPerWarp; ++u)
+                    for (int u = 0; u < NR; ++u)
                         if (u < myrows) acc[u] = fma(Abase[(int64_t)(base + u * kWarps) * lda + col], xv, acc[u]);
                 }
             }
             // lane l ends with row u(l)'s sum, bit for bit the warp_sum of that row
-            const T sum = transpose_sum<T, kRowsPerWarp>(acc, lane);
-            const int u = transpose_row<kRowsPerWarp>(lane);
-            if (transpose_rep<kRowsPerWarp>(lane) && u < myrows) {
+            const T sum = transpose_sum<T, NR>(acc, lane);
+            const int u = transpose_row<NR>(lane);
+            if (transpose_rep<NR>(lane) && u < myrows) {
                 const int q = base + u * kWarps;
                 const T r = bts[q] - sum;
                 const T w = w2s[q];
@@ -770,6 +790,21 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     finish(p.info, status, k);
 }
 
+// Shared-memory GEMV loop: rows a warp scores in one pass, the smallest of
+// 1, 2, 4, 8 covering its share of the CTA's rows (a transposed butterfly
+// over N rows costs N + 4 adds, FP64 ones on the slow pipe).
+const void* gemv_kernel(int dtype, int rows_per_cta) {
+    const int rpw = (rows_per_cta + kWarps - 1) / kWarps;
+    const int nr = rpw <= 1 ? 1 : rpw <= 2 ? 2 : rpw <= 4 ? 4 : kRowsPerWarp;
+    const bool f64 = dtype == CSK_F64;
+    switch (nr) {
+        case 1: return f64 ? (const void*)k_iterate_gemv<double, 1> : (const void*)k_iterate_gemv<float, 1>;
+        case 2: return f64 ? (const void*)k_iterate_gemv<double, 2> : (const void*)k_iterate_gemv<float, 2>;
+        case 4: return f64 ? (const void*)k_iterate_gemv<double, 4> : (const void*)k_iterate_gemv<float, 4>;
+        default: return f64 ? (const void*)k_iterate_gemv<double, 8> : (const void*)k_iterate_gemv<float, 8>;
+    }
+}
+
 const void* stream_kernel(int dtype, int cpl) {
     const bool f64 = dtype == CSK_F64;
     switch (cpl) {
@@ -1068,8 +1103,7 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
     else if (stream) fn = const_cast<void*>(stream_kernel(p.dtype, cfg.stream_cpl));
     else if (reg) fn = const_cast<void*>(reg_kernel(cfg.reg_rpw, cfg.reg_cpl));
-    else if (p.dtype == CSK_F64) fn = (void*)k_iterate_gemv<double>;
-    else fn = (void*)k_iterate_gemv<float>;
+    else fn = const_cast<void*>(gemv_kernel(p.dtype, cfg.rows_per_cta));
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = ensure_smem_attr(fn, cfg.smem);
     if (e != cudaSuccess) return e;

@@ -86,20 +86,32 @@ __device__ __forceinline__ void warp_reduce(Red<float>& c) {
 // FP64 warp argmax with integer comparisons: non-negative doubles order as
 // their bit patterns, so the key becomes a monotone 64-bit code (NaN highest,
 // "no candidate" lowest) compared on the integer pipe -- this GPU runs FP64
-// at 1/64 of the FP32 rate.  Same ordering as better(); the statistic is
-// summed with the same shuffle tree as before.
-__device__ __forceinline__ void warp_reduce(Red<double>& c) {
+// at 1/64 of the FP32 rate.  Same ordering as better().  The statistic is
+// left alone (see warp_reduce below).
+__device__ __forceinline__ void warp_argmax(Red<double>& c) {
     uint64_t code = key_code(c.key);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const uint64_t c2 = __shfl_xor_sync(0xffffffffu, code, o);
         const double a2 = __shfl_xor_sync(0xffffffffu, c.alpha, o);
         const int32_t i2 = __shfl_xor_sync(0xffffffffu, c.idx, o);
-        c.stat += __shfl_xor_sync(0xffffffffu, c.stat, o);
         if (c2 > code || (c2 == code && i2 < c.idx)) { code = c2; c.alpha = a2; c.idx = i2; }
     }
     c.key = code == ~0ull ? (double)NAN
           : code == 0ull ? -1.0 : __longlong_as_double((long long)(code - 1ull));
+}
+
+// The FP64 statistic summed by the butterfly, skipped when every lane holds
+// +0 (the sum would be +0): FP64 adds occupy the slow pipe, and in most warps
+// of a step only a few lanes carry a share of ||x - x*||^2.
+__device__ __forceinline__ double warp_sum_nonzero(double v) {
+    if (!__any_sync(0xffffffffu, __double_as_longlong(v) != 0)) return v;
+    return warp_sum(v);
+}
+
+__device__ __forceinline__ void warp_reduce(Red<double>& c) {
+    warp_argmax(c);
+    c.stat = warp_sum_nonzero(c.stat);
 }
 
 // --------------------------------------------------- row sums of a warp
@@ -155,6 +167,7 @@ struct Pow2Rows {   // smallest of 1, 2, 4, 8 holding R rows
 template <typename T, int W = 8>
 struct RedShared {
     Red<T> buf[2][W];          // W >= warps per CTA
+    Red<T> res[2];             // FP64: the combined result
 };
 
 template <typename T, int W>
@@ -168,6 +181,28 @@ __device__ __forceinline__ Red<T> block_reduce(Red<T> c, RedShared<T, W>& sh, in
     else { r.key = T(-1); r.alpha = T(0); r.stat = T(0); r.idx = INT_MAX; }
     par ^= 1;
     warp_reduce(r);
+    return r;
+}
+
+// FP64: warp 0 alone combines the warps' partials (so the FP64 adds run on
+// one warp instead of all of them) and shares the result through shared
+// memory, at the price of a second barrier.
+template <int W>
+__device__ __forceinline__ Red<double> block_reduce(Red<double> c, RedShared<double, W>& sh, int& par) {
+    warp_reduce(c);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.buf[par][warp] = c;
+    __syncthreads();
+    if (warp == 0) {
+        Red<double> r;
+        if (lane < (int)(blockDim.x >> 5)) r = sh.buf[par][lane];
+        else { r.key = -1.0; r.alpha = 0.0; r.stat = 0.0; r.idx = INT_MAX; }
+        warp_reduce(r);
+        if (lane == 0) sh.res[par] = r;
+    }
+    __syncthreads();
+    const Red<double> r = sh.res[par];
+    par ^= 1;
     return r;
 }
 
