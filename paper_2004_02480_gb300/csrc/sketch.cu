@@ -551,9 +551,13 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
-    // warps per bucket: one per column chunk, at most 4
-    auto warps_for = [&](int cw) { int w = (n + cw - 1) / cw; return w < 1 ? 1 : (w > 4 ? 4 : w); };
-    const int bs = 32 * warps_for(128);
+    // warps per bucket: one per column chunk (128 columns, or 64 for FP64
+    // rows of at most 64 columns, where a second 64-column half of the chunk
+    // would only add zeros on the slow FP64 pipe), at most 4
+    const bool narrow64 = dtype == CSK_F64 && n <= 64;
+    const int cw = narrow64 ? 64 : 128;
+    const int warps = (n + cw - 1) / cw < 1 ? 1 : ((n + cw - 1) / cw > 4 ? 4 : (n + cw - 1) / cw);
+    const int bs = 32 * warps;
     // as many CTAs as stay resident (they claim the buckets), at most d
     auto grid_for = [&](const void* fn, int* g) -> cudaError_t {
         int per_sm = 0;
@@ -574,7 +578,8 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
                            d, seed, (float*)At, N2, s.cnt + d);
     } else {
         const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
-        const auto fn = vec ? k_segsum<double, 2, 2, 4> : k_segsum<double, 1, 4, 4>;
+        const auto fn = vec ? (narrow64 ? k_segsum<double, 2, 1, 4> : k_segsum<double, 2, 2, 4>)
+                            : (narrow64 ? k_segsum<double, 1, 2, 4> : k_segsum<double, 1, 4, 4>);
         e = grid_for((const void*)fn, &blocks);
         if (e == cudaSuccess)
             e = launch_dep(fn, blocks, bs, st, (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off,
