@@ -5,13 +5,14 @@
 //   k_hist        cnt[j] = #{i : h(i) = j}            (warp-aggregated atomics)
 //   k_scan_*      off = exclusive prefix sum of cnt   (off[d] = m)
 //   k_scatter     perm_tmp: rows grouped by bucket (arbitrary order inside)
-//   k_segsum      one CTA per bucket: puts the bucket's rows in ascending
+//   k_segsum      resident CTAs claim buckets: each puts a bucket's rows in ascending
 //                 order in shared memory (writing perm, the rows in (h(i), i)
 //                 order -- unique, so independent of the atomics' order),
 //                 then At_j = sum_{p in bucket j, ascending} D_ii A_i and
 //                 ||At_j||^2 in FP64: a warp per 128-column chunk, 128-bit
 //                 loads, 4 rows in flight per warp
-//   k_segsum_b    Bt likewise (right-hand sides), one warp per bucket
+//   k_segsum_b1   bt likewise (one right-hand side), a warp per 8 buckets
+//   k_segsum_b    Bt likewise (several right-hand sides), a warp per bucket
 #include <climits>
 #include <cstdio>
 
@@ -355,8 +356,10 @@ __device__ __forceinline__ double seg_chunk(const T* __restrict__ src, int64_t l
 // the bucket's rows in that order; the FP64 row norm is combined across
 // warps in a fixed order.
 template <typename T, int V, int CPL, int U>
-// 10 CTAs per SM in FP32 (48 registers; at 56 the kernel ran markedly slower), 7 in FP64
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 10 : 7)
+// 10 CTAs per SM in FP32 (48 registers; at 56 the kernel ran markedly slower), 7 in FP64;
+// the one-warp FP64 variants for narrow (U = 8) or 129..256-column rows
+// (CPL > 2) get room for their loads
+__global__ void __launch_bounds__(128, (U > 4 || CPL * V > 4) ? 4 : (sizeof(T) == 4 ? 10 : 7))
 k_segsum(const T* __restrict__ A, int64_t lda, int n, int64_t m,
          const int32_t* __restrict__ perm_tmp, int32_t* __restrict__ perm,
          const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ At,
@@ -424,11 +427,69 @@ k_segsum(const T* __restrict__ A, int64_t lda, int n, int64_t m,
     }
 }
 
-// Signed sums of the right-hand sides, one warp per bucket (grid-stride),
-// ascending row order.  One right-hand side: the lanes load 32 rows' values
-// at once and the sum takes them in order through shuffles, so the loads of
-// a bucket overlap while the order stays fixed.  Several: lanes run over the
-// columns, rows in order, 4 rows in flight.
+// Signed sums of the right-hand sides in ascending row order.
+//
+// FP64, one right-hand side (k_segsum_b1): a warp takes kBGroup buckets at a time
+// and lane l < kBGroup sums bucket l of the group.  Each round the warp loads
+// the next 32 rows of every bucket of the group (lane q takes row q of each,
+// coalesced within a bucket), puts the signed values in a warp-private
+// shared tile, and lanes 0..kBGroup-1 add their bucket's values in order.
+// One add instruction thus serves kBGroup buckets: this GPU issues a warp's
+// FP64 instruction at the same cost however few lanes are active.
+//
+// FP32 (k_segsum_b): one warp per bucket.  One right-hand side: the lanes
+// load 32 rows' values at once and the sum takes them in order through
+// shuffles.  Several: lanes over the columns, rows in order, 4 rows in
+// flight.
+constexpr int kBGroup = 8;
+constexpr int kBWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kBWarps)
+k_segsum_b1(const T* __restrict__ B, int64_t ldb, const int32_t* __restrict__ perm,
+            const int32_t* __restrict__ off, int d, uint64_t seed, T* __restrict__ Bt) {
+    pdl_wait();
+    __shared__ T tile[kBWarps][kBGroup][33];   // padded: lanes 0..7 read distinct banks
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * kBWarps;
+    for (int64_t j0 = ((int64_t)blockIdx.x * kBWarps + warp) * kBGroup; j0 < d; j0 += nwarps * kBGroup) {
+        // lane g <= kBGroup reads off[j0 + g]; bucket g of the group spans [p0_g, p0_{g+1})
+        const int64_t jl = j0 + (lane <= kBGroup ? lane : kBGroup);
+        const int32_t offl = off[jl < d ? jl : d];
+        const int32_t mycnt = __shfl_down_sync(0xffffffffu, offl, 1) - offl;   // lanes < kBGroup
+        int32_t p0[kBGroup], cnt[kBGroup];
+        int32_t maxcnt = 0;
+#pragma unroll
+        for (int g = 0; g < kBGroup; ++g) {
+            p0[g] = __shfl_sync(0xffffffffu, offl, g);
+            cnt[g] = __shfl_sync(0xffffffffu, offl, g + 1) - p0[g];   // 0 past d
+            maxcnt = max(maxcnt, cnt[g]);
+        }
+        T acc = T(0);
+        for (int32_t pb = 0; pb < maxcnt; pb += 32) {
+            int32_t row[kBGroup];
+#pragma unroll
+            for (int g = 0; g < kBGroup; ++g) row[g] = pb + lane < cnt[g] ? perm[p0[g] + pb + lane] : -1;
+#pragma unroll
+            for (int g = 0; g < kBGroup; ++g) {
+                T v = T(0);
+                if (row[g] >= 0) {
+                    v = B[(int64_t)row[g] * ldb];
+                    if (row_negative(row_hash(seed, (uint64_t)row[g]))) v = -v;
+                }
+                tile[warp][g][lane] = v;
+            }
+            __syncwarp();
+            if (lane < kBGroup) {
+                const int32_t c = min(32, mycnt - pb);
+                for (int q = 0; q < c; ++q) acc += tile[warp][lane][q];
+            }
+            __syncwarp();
+        }
+        if (lane < kBGroup && j0 + lane < d) Bt[j0 + lane] = acc;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __restrict__ perm,
@@ -551,42 +612,54 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
-    // warps per bucket: one per column chunk (128 columns, or 64 for FP64
-    // rows of at most 64 columns, where a second 64-column half of the chunk
-    // would only add zeros on the slow FP64 pipe), at most 4
-    const bool narrow64 = dtype == CSK_F64 && n <= 64;
-    const int cw = narrow64 ? 64 : 128;
+    // warps per bucket: one per column chunk, at most 4.  FP32: 128-column
+    // chunks.  FP64 adds occupy the slow pipe at the same cost whatever the
+    // lanes hold, so an FP64 row of up to 256 columns is one chunk sized to
+    // it (no chunk half made of zeros), and a row of at most 64 columns keeps
+    // 8 rows in flight instead of 4 (a warp moves few bytes per row).
+    int cw = 128;
+    const void* fn = nullptr;
+    if (dtype == CSK_F32) {
+        const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
+        fn = vec ? (const void*)k_segsum<float, 4, 1, 4> : (const void*)k_segsum<float, 1, 4, 4>;
+    } else {
+        const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
+        if (vec) {
+            const int c2 = (n + 63) / 64;                 // double2 chunks per lane to cover the row
+            fn = c2 <= 1 ? (const void*)k_segsum<double, 2, 1, 8>
+               : c2 == 2 ? (const void*)k_segsum<double, 2, 2, 4>
+               : c2 == 3 ? (const void*)k_segsum<double, 2, 3, 4>
+               : c2 == 4 ? (const void*)k_segsum<double, 2, 4, 4> : (const void*)k_segsum<double, 2, 2, 4>;
+            cw = c2 <= 4 ? 64 * (c2 < 1 ? 1 : c2) : 128;
+        } else {
+            fn = n <= 64 ? (const void*)k_segsum<double, 1, 2, 8> : (const void*)k_segsum<double, 1, 4, 4>;
+            cw = n <= 64 ? 64 : 128;
+        }
+    }
     const int warps = (n + cw - 1) / cw < 1 ? 1 : ((n + cw - 1) / cw > 4 ? 4 : (n + cw - 1) / cw);
     const int bs = 32 * warps;
     // as many CTAs as stay resident (they claim the buckets), at most d
-    auto grid_for = [&](const void* fn, int* g) -> cudaError_t {
-        int per_sm = 0;
-        const cudaError_t ce = cached_occupancy(fn, bs, 0, &per_sm);
-        if (ce != cudaSuccess) return ce;
-        const int64_t r = (int64_t)(per_sm > 0 ? per_sm : 1) * di.sms;
-        *g = (int)(r < d ? r : d);
-        return cudaSuccess;
-    };
-    cudaError_t e;
-    int blocks = 0;
-    if (dtype == CSK_F32) {
-        const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
-        const auto fn = vec ? k_segsum<float, 4, 1, 4> : k_segsum<float, 1, 4, 4>;
-        e = grid_for((const void*)fn, &blocks);
-        if (e == cudaSuccess)
-            e = launch_dep(fn, blocks, bs, st, (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off,
-                           d, seed, (float*)At, N2, s.cnt + d);
-    } else {
-        const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
-        const auto fn = vec ? (narrow64 ? k_segsum<double, 2, 1, 4> : k_segsum<double, 2, 2, 4>)
-                            : (narrow64 ? k_segsum<double, 1, 2, 4> : k_segsum<double, 1, 4, 4>);
-        e = grid_for((const void*)fn, &blocks);
-        if (e == cudaSuccess)
-            e = launch_dep(fn, blocks, bs, st, (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off,
-                           d, seed, (double*)At, N2, s.cnt + d);
-    }
+    int per_sm = 0;
+    cudaError_t e = cached_occupancy(fn, bs, 0, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * di.sms;
+    const int blocks = (int)(resident < d ? resident : d);
+    if (dtype == CSK_F32)
+        e = launch_dep(reinterpret_cast<decltype(&k_segsum<float, 4, 1, 4>)>(const_cast<void*>(fn)), blocks,
+                       bs, st, (const float*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed, (float*)At,
+                       N2, s.cnt + d);
+    else
+        e = launch_dep(reinterpret_cast<decltype(&k_segsum<double, 2, 2, 4>)>(const_cast<void*>(fn)), blocks,
+                       bs, st, (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed,
+                       (double*)At, N2, s.cnt + d);
     note_launches(1);
-    if (e == cudaSuccess && B && nrhs > 0) {
+    if (e == cudaSuccess && B && nrhs == 1 && dtype == CSK_F64) {
+        int64_t bblocks = ((int64_t)d + kBWarps * kBGroup - 1) / (kBWarps * kBGroup);
+        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
+        e = launch_dep(k_segsum_b1<double>, (int)bblocks, 32 * kBWarps, st, (const double*)B, ldb,
+                       s.perm, s.off, d, seed, (double*)Bt);
+        note_launches(1);
+    } else if (e == cudaSuccess && B && nrhs > 0) {
         int64_t bblocks = ((int64_t)d + 7) / 8;
         if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
         if (dtype == CSK_F32)

@@ -95,7 +95,10 @@ def test_sketch_fp32_bit_exact(csk, m, n, d, R):
     assert np.all(np.abs(s.At.cpu().numpy() - At64) <= cnt * 2.0 ** -24 * absum + 1e-30)
 
 
-@pytest.mark.parametrize("m,n,d", [(2000, 50, 500), (999, 7, 100), (4000, 130, 4000)])
+@pytest.mark.parametrize("m,n,d", [(2000, 50, 500), (999, 7, 100), (4000, 130, 4000),
+                                   # FP64 chunk shapes: 64, 128, 192, 256 columns, several warps, scalar
+                                   (3000, 64, 700), (3000, 128, 700), (3000, 200, 900), (3000, 256, 900),
+                                   (3000, 300, 900), (3000, 65, 800)])
 def test_sketch_fp64_bit_exact(csk, m, n, d):
     s_ = synth.gaussian_system(m, n, m, np.float64)
     s = _gpu_sketch(csk, s_.A, s_.b, d, 3)
