@@ -60,12 +60,32 @@ __device__ __forceinline__ Slot* mailbox(Slot* slots, uint32_t round, int dest, 
     return slots + ((size_t)(round & 1u) * G + dest) * G + src;
 }
 
+// Rows the chosen candidate's data will be read from after an exchange: the
+// bytes [base + idx * ld, + bytes) of row idx < rows.  Each polling warp
+// prefetches them into L1 for its own best candidate, before the CTA-wide
+// reduction picks the winner among the warps' bests (the winner is always one
+// of them), so the read after the exchange finds them on chip.
+struct RowPrefetch {
+    const char* base = nullptr;
+    int64_t ld = 0;            // bytes between rows
+    int bytes = 0;             // <= 32 lines of 128 bytes
+    int rows = 0;
+};
+
+__device__ __forceinline__ void prefetch_row(const RowPrefetch& pf, int32_t idx) {
+    if (!pf.base || (uint32_t)idx >= (uint32_t)pf.rows) return;
+    const uintptr_t r = reinterpret_cast<uintptr_t>(pf.base) + (uintptr_t)idx * (uintptr_t)pf.ld;
+    const uintptr_t a = (r & ~(uintptr_t)127) + 128u * (threadIdx.x & 31);
+    if (a < r + (uintptr_t)pf.bytes) asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+
 // FP32: four stamped words per slot.
 // With `acquire`, every polling thread fences after seeing the new round, so
 // plain data the other CTAs stored before publishing is visible afterwards.
 __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>& c,
                                          int64_t spin_limit, int fault_inject, csk_info* info,
-                                         RedShared<float>& sh, int& par, bool acquire = false) {
+                                         RedShared<float>& sh, int& par, bool acquire = false,
+                                         const RowPrefetch& pf = RowPrefetch()) {
     const int G = gridDim.x, b = blockIdx.x;
     const uint64_t stamp = (uint64_t)(round + 1u) << 32;
     if (!(fault_inject && b == 0))
@@ -99,7 +119,13 @@ __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>
         if (threadIdx.x == 0) set_status_once(info, CSK_ETIMEOUT);
         return false;
     }
-    c = block_reduce(g, sh, par);
+    if (pf.base) {
+        warp_reduce(g);
+        prefetch_row(pf, g.idx);
+        c = block_combine(g, sh, par);
+    } else {
+        c = block_reduce(g, sh, par);
+    }
     return true;
 }
 
@@ -909,7 +935,12 @@ k_iterate_gram(IterProblem p, int R) {
                 c.stat += t * t;
             }
         c = block_reduce(c, sh, par);
-        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
+        RowPrefetch gpf;          // this CTA's slice of G[i_k, :], read from HBM after the exchange
+        gpf.base = reinterpret_cast<const char*>(p.G + r0);
+        gpf.ld = p.ldg * (int64_t)sizeof(float);
+        gpf.bytes = nr * (int)sizeof(float) <= 32 * 128 ? nr * (int)sizeof(float) : 32 * 128;
+        gpf.rows = d;
+        if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par, false, gpf)) {
             status = CSK_ETIMEOUT;
             break;
         }

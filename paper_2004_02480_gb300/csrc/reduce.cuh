@@ -206,6 +206,21 @@ __device__ __forceinline__ Red<double> block_reduce(Red<double> c, RedShared<dou
     return r;
 }
 
+// The cross-warp step alone, for a candidate (statistic included) that a
+// warp_reduce has already made uniform across each warp.
+template <typename T, int W>
+__device__ __forceinline__ Red<T> block_combine(const Red<T>& c, RedShared<T, W>& sh, int& par) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.buf[par][warp] = c;
+    __syncthreads();
+    Red<T> r;
+    if (lane < (int)(blockDim.x >> 5)) r = sh.buf[par][lane];
+    else { r.key = T(-1); r.alpha = T(0); r.stat = T(0); r.idx = INT_MAX; }
+    par ^= 1;
+    warp_reduce(r);
+    return r;
+}
+
 // The same, for partials whose candidate is already uniform across each warp
 // (Phase A: every lane of a warp holds the row results of that warp), so only
 // the statistic needs a warp sum before the cross-warp step.
