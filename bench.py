@@ -14,6 +14,7 @@ independent system (weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload {c1,precision,batched,serving}   # the other configurations
+    python bench.py --workload noisy     # an inconsistent b, residual stopping rule
 
 `--impl reference` times the plain CPU oracle (the paper's method restated
 in C, FP64) on the same workload on this machine's host cores.
@@ -255,6 +256,57 @@ def run_c1(args):
     return 0
 
 
+def run_noisy(args):
+    """Inconsistent system (outside the paper's consistent setting): the
+    100000x500 FP32 workload with b = A x* + e, e iid Gaussian at 1e-3 of
+    rms(A x*); no x*, so the loop stops on ||bt - At x||^2 / ||bt||^2 <= 1e-5,
+    about ten times the least-squares floor of the sketched system."""
+    import torch
+    from paper_2004_02480_gb300 import csk, synth
+    csk.lib()
+    dev = torch.device("cuda", 0)
+    m, n, d, tol = M, N_COLS, D, 1e-5
+    s = synth.noisy_system(m, n, 0, 1e-3, np.float32)
+    A, b = (torch.from_numpy(v).to(dev) for v in (s.A, s.b))
+    from paper_2004_02480_gb300 import autotune
+    p = csk.csk_params_default(d=d, seed=0, tol=tol, path=csk.GEMV)
+    autotune.tune_solve(A, b, p)                      # grid and loop variant, untimed
+    ws = csk._workspace(csk.csk_solve_workspace_size(m, n, csk.CSK_F32, p), dev)
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    info = torch.zeros(64, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        csk.csk_solve(A, b, p, x_out=x, info=info, ws=ws, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch, 2)
+    e0.record()
+    for _ in range(args.steps):
+        csk.csk_solve(A, b, p, x_out=x, info=info, ws=ws, sync=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    r = csk.read_info(info)
+    # least-squares floor of the sketched system (no x reaches a smaller residual)
+    sk = csk.csk_sketch(A, d, 0, b)
+    At, bt = sk.At.double().cpu().numpy(), sk.bt.double().cpu().numpy().ravel()
+    xls = np.linalg.lstsq(At, bt, rcond=None)[0]
+    floor = float(np.sum((bt - At @ xls) ** 2) / np.sum(bt * bt))
+    xv = x.double().cpu().numpy()
+    print(json.dumps({
+        "metric": "time-to-residual tol (ms), inconsistent system, no x*", "value": ms, "unit": "ms",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1); b = A x* + 1e-3 rms(A x*) noise)",
+        "config": {"workload": f"A {m}x{n} FP32, d={d}, b = A x* + e (relative noise 1e-3), no x*, "
+                               f"stop at ||bt - At x||^2/||bt||^2 <= {tol}", "grid": r["grid"],
+                   "variant": int(p.gemv_variant)},
+        "whole_solve_us_per_step": 1e3 * ms / (r["iters"] + 1),
+        "status": r["status"], "iters": r["iters"], "resid2": r["resid"] ** 2,
+        "ls_floor_resid2": floor, "resid2_over_floor": r["resid"] ** 2 / floor,
+        "rel_err_vs_noiseless_x": float(np.linalg.norm(xv - s.x_star) / np.linalg.norm(s.x_star)),
+        "rel_err_vs_sketched_ls": float(np.linalg.norm(xv - xls) / np.linalg.norm(xls))}),
+        flush=True)
+    return 0
+
+
 def run_precision(args):
     """precision form: A 1e6x1000 FP32 = G diag(sigma) Q, kappa 1e3, d = 20000,
     split-BF16 Gram, FP64 refresh every 100 steps."""
@@ -411,10 +463,10 @@ def main():
     ap.add_argument("--grid", type=int, default=0, help="loop CTA count (0 = autotune)")
     ap.add_argument("--variant", type=int, default=0, help="loop variant 1-3 (0 = autotune)")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "c1", "precision", "batched", "serving"],
+                    choices=["plain", "c1", "precision", "batched", "serving", "noisy"],
                     help="plain: the 100000x500 line (default); c1: 2000x50 FP64; precision: "
                          "1e6x1000 kappa 1e3 GRAM; batched: 256 systems x 64 RHS; serving: "
-                         "Poisson arrivals")
+                         "Poisson arrivals; noisy: 100000x500 with an inconsistent b")
     ap.add_argument("--seconds", type=float, default=60.0, help="serving: arrival window")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
     args = ap.parse_args()
@@ -422,7 +474,7 @@ def main():
         return run_reference(args)
     if args.workload != "plain":
         return {"c1": run_c1, "precision": run_precision, "batched": run_batched,
-                "serving": run_serving}[args.workload](args)
+                "serving": run_serving, "noisy": run_noisy}[args.workload](args)
 
     import torch
     import torch.distributed as dist

@@ -22,10 +22,11 @@ namespace {
 constexpr int64_t kNoAllocMaxRows = 1 << 20;      // m  <= 1,048,576
 constexpr int64_t kNoAllocMaxBuckets = 1 << 18;   // d  <=   262,144
 
-// Same carving as carve_sort_scratch() for the maximum sizes.
+// Same carving as carve_sort_scratch() for the maximum sizes (a call that
+// needs more is refused with CSK_ENOMEM, and a test runs the maximum sizes).
 constexpr int64_t kScanTileRows = 4096;
 constexpr int64_t kNoAllocBytes =
-    (kNoAllocMaxBuckets * 4 + 255) / 256 * 256 +                 // cnt
+    ((kNoAllocMaxBuckets + 1) * 4 + 255) / 256 * 256 +           // cnt (+ claim counter)
     ((kNoAllocMaxBuckets + 1) * 4 + 255) / 256 * 256 +           // off
     2 * ((kNoAllocMaxRows * 4 + 255) / 256 * 256) +              // perm_tmp, perm
     (((kNoAllocMaxBuckets + kScanTileRows - 1) / kScanTileRows) * 4 + 255) / 256 * 256;

@@ -17,6 +17,10 @@ Recipes (sizes are the caller's):
 * :func:`gaussian_multi_rhs`   -- A iid N(0, 1), X* (n x R) iid N(0, 1), B = A X*.
 * :func:`batched_shapes`       -- (m, n) pairs with m log-uniform and n
                                   uniform-integer.
+* :func:`noisy_system`         -- an inconsistent system: A, x* as in
+                                  :func:`gaussian_system`, b = A x* + e with e
+                                  iid N(0, (noise * rms(A x*))^2) from a second
+                                  stream.
 """
 from __future__ import annotations
 
@@ -43,6 +47,18 @@ def gaussian_system(m: int, n: int, seed: int, dtype=np.float64) -> System:
     xs = g.standard_normal(n)
     b = A.astype(np.float64, copy=False) @ xs
     return System(np.ascontiguousarray(A, dtype=dtype), b.astype(dtype), xs)
+
+
+def noisy_system(m: int, n: int, seed: int, noise: float, dtype=np.float64) -> System:
+    """A, x* as gaussian_system(m, n, seed); b = A x* + e, e iid Gaussian with
+    standard deviation noise * rms(A x*), drawn from a stream of its own; b in
+    binary64 then cast.  x_star is the x* the noise was added to (no longer a
+    solution)."""
+    s = gaussian_system(m, n, seed, dtype)
+    g = np.random.default_rng(np.random.SeedSequence([int(seed), 0x2004_02480, 1]))
+    ax = s.A.astype(np.float64, copy=False) @ s.x_star
+    b = ax + noise * np.sqrt(np.mean(ax * ax)) * g.standard_normal(m)
+    return System(s.A, b.astype(dtype), s.x_star)
 
 
 def gaussian_multi_rhs(m: int, n: int, R: int, seed: int, dtype=np.float32) -> System:

@@ -392,3 +392,64 @@ def test_fp64_check_widens_subnormals_exactly(csk):
     want = np.sqrt(np.sum(r * r) / np.sum(b.astype(np.float64) ** 2))
     assert abs(info["resid"] - want) <= 1e-13 * want
     assert info["empty_rows"] == 0
+
+
+def _ls_floor(At, bt):
+    """||bt - At x_LS||^2 / ||bt||^2: no x reaches a smaller residual."""
+    xls = np.linalg.lstsq(At, bt, rcond=None)[0]
+    return float(np.sum((bt - At @ xls) ** 2) / np.sum(bt * bt))
+
+
+def test_inconsistent_system_residual_stop_fp64(csk):
+    """Inconsistent b = A x* + e (relative noise 1e-3), no x*: the loop stops
+    on ||bt - At x||^2 / ||bt||^2 <= tol.  Above the least-squares floor of
+    the sketched system the GPU follows the oracle's row sequence and stops at
+    its IT; below the floor neither can stop (no x beats the least-squares
+    residual), both run to the cap and end above the floor."""
+    m, n, d, seed = 2000, 50, 500, 8
+    s = synth.noisy_system(m, n, seed, 1e-3, np.float64)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, d)
+    floor = _ls_floor(At, bt)
+    assert 1e-7 < floor < 1e-5
+    # reachable: 10 x the floor
+    tol = 10 * floor
+    ik = torch.full((4000,), -1, dtype=torch.int32, device=DEV)
+    p = csk.csk_params_default(d=d, seed=seed, tol=tol, ik_log=ik.data_ptr(), ik_log_len=4000)
+    x, info = csk.csk_solve(_to(s.A), _to(s.b), p)
+    ref = oracle.mwrk(At, bt, tol=tol, log_len=4000)
+    assert info["status"] == 0 and info["resid"] ** 2 <= tol * (1 + 1e-9)
+    assert abs(info["iters"] - ref.iters) <= 1
+    k = min(info["iters"], ref.iters)
+    assert np.array_equal(ik.cpu().numpy()[:k], ref.ik[:k])
+    if info["iters"] == ref.iters:
+        assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    # unreachable: a tenth of the floor, 3000-step cap
+    p2 = csk.csk_params_default(d=d, seed=seed, tol=floor / 10, max_iter=3000)
+    x2, info2 = csk.csk_solve(_to(s.A), _to(s.b), p2)
+    ref2 = oracle.mwrk(At, bt, tol=floor / 10, max_iter=3000)
+    assert info2["status"] == 1 and info2["iters"] == 3000 and ref2.iters == 3000
+    for res in (info2["resid"] ** 2, float(np.sum((bt - At @ ref2.x) ** 2) / np.sum(bt * bt))):
+        assert floor * (1 - 1e-9) <= res <= 10 * floor
+
+
+def test_inconsistent_system_residual_stop_fp32(csk):
+    """FP32, 20000 x 200, d = 2000, relative noise 1e-3, no x*, tol ten times
+    the least-squares floor: the GPU (register or shared-memory loop) follows
+    the oracle's rows on the bit-identical FP32 sketch up to the first
+    near-tie (gap 1e-3) and stops within 2 % of its IT, above the floor."""
+    m, n, d, seed = 20000, 200, 2000, 4
+    s = synth.noisy_system(m, n, seed, 1e-3, np.float32)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    At, bt = At32.astype(np.float64), bt32.astype(np.float64)
+    floor = _ls_floor(At, bt)
+    tol = 10 * floor
+    ik = torch.full((20000,), -1, dtype=torch.int32, device=DEV)
+    p = csk.csk_params_default(d=d, seed=seed, tol=tol, ik_log=ik.data_ptr(), ik_log_len=20000)
+    x, info = csk.csk_solve(_to(s.A), _to(s.b), p)
+    ref = oracle.mwrk(At, bt, tol=tol, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and ref.status == 0
+    assert floor * (1 - 1e-6) <= info["resid"] ** 2 <= tol * (1 + 1e-3)
+    assert abs(info["iters"] - ref.iters) <= max(2, 0.02 * ref.iters)
+    _compare_prefix(ik.cpu().numpy(), ref, 1e-3)

@@ -30,7 +30,8 @@ def test_noalloc_sketch_matches_workspace_sketch_twice(csk):
     dev = "cuda:0"
     g = torch.Generator(device=dev).manual_seed(123)
     cases = [(200_000, 300, 3000, 2, torch.float32, 7),   # several scan tiles, b with 2 RHS
-             (50_000, 33, 700, 1, torch.float64, 8)]      # ragged n, FP64
+             (50_000, 33, 700, 1, torch.float64, 8),      # ragged n, FP64
+             (1 << 20, 4, 1 << 18, 1, torch.float32, 9)]  # the largest m and d the scratch holds
     for m, n, d, R, dt, seed in cases:
         A = torch.randn((m, n), generator=g, device=dev, dtype=dt)
         b = torch.randn((m, R), generator=g, device=dev, dtype=dt)
