@@ -18,11 +18,14 @@
 // statistic are FP32, and a slot is four 64-bit words that each carry the
 // round stamp next to 32 bits of payload, so one relaxed load of each word
 // both detects the new round and delivers its data (one L2 round trip).
-// FP64 solves use FP64 throughout and a release/acquire-stamped slot.
+// FP64 solves use FP64 values throughout (compared and tested through
+// integer codes of their bit patterns) and a slot of eight stamped words.
 //
-// GEMV path: r = bt - At x is recomputed every step (Algorithm 1 as printed);
-// x is replicated in every CTA's shared memory and, when it fits, the CTA's
-// rows of At stay resident in shared memory for the whole solve.
+// GEMV path: r = bt - At x is recomputed every step (Algorithm 1 as printed).
+// Three loops: the CTA's rows of At in registers with x in every warp's
+// registers (k_iterate_gemv_reg, FP32), rows and x in shared memory
+// (k_iterate_gemv), or rows streamed from global memory through a bulk-copy
+// ring every step when they fit neither (k_iterate_gemv_stream: MWRK on A).
 // GRAM path: r lives in shared memory, r -= alpha * G[i_k, :] with
 // G = At At^T, r_{i_k} = 0 exactly; x is split by columns across CTAs; every
 // refresh_every steps r is recomputed as bt - At x with FP64 accumulation.
