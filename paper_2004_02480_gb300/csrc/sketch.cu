@@ -2,17 +2,23 @@
 // "Initialize"; S = Phi D of Definition 1) on sm_103a.
 //
 // Pipeline (all integer work bit-exact, FP work in a fixed order):
-//   k_hist        cnt[j] = #{i : h(i) = j}            (warp-aggregated atomics)
+//   k_hist        cnt[j] = #{i : h(i) = j}, and row i's slot in its bucket
+//                 (warp-aggregated atomics)
 //   k_scan_*      off = exclusive prefix sum of cnt   (off[d] = m)
-//   k_scatter     perm_tmp: rows grouped by bucket (arbitrary order inside)
-//   k_segsum      resident CTAs claim buckets: each puts a bucket's rows in ascending
-//                 order in shared memory (writing perm, the rows in (h(i), i)
-//                 order -- unique, so independent of the atomics' order),
-//                 then At_j = sum_{p in bucket j, ascending} D_ii A_i and
-//                 ||At_j||^2 in FP64: a warp per 128-column chunk, 128-bit
-//                 loads, 4 rows in flight per warp
-//   k_segsum_b1   bt likewise (one right-hand side), a warp per 8 buckets
-//   k_segsum_b    Bt likewise (several right-hand sides), a warp per bucket
+//   k_scatter     perm_tmp[off[h(i)] + slot(i)] = i: rows grouped by bucket
+//                 (in the atomics' order inside a bucket)
+//   k_segsum      resident CTAs claim buckets: each puts a bucket's rows in
+//                 ascending order in shared memory (writing perm, the rows in
+//                 (h(i), i) order -- unique, so independent of the atomics'
+//                 order), then At_j = sum_{p in bucket j, ascending} D_ii A_i
+//                 and ||At_j||^2 in FP64: a warp per column chunk (128
+//                 columns in FP32; up to 256, sized to the row, in FP64),
+//                 16-byte loads, 4 (narrow FP64 rows: 8) rows in flight
+//   k_segsum_b1   bt likewise, FP64 with one right-hand side, a warp per 8
+//                 buckets
+//   k_segsum_b    Bt likewise otherwise, a warp per bucket
+// The kernels after k_hist launch with programmatic stream serialization and
+// wait for their predecessor inside (pdl_wait).
 #include <climits>
 #include <cstdio>
 
