@@ -318,6 +318,8 @@ def run_precision(args):
     xs = xs64.float()
     p = csk.csk_params_default(d=d, seed=0, path=csk.GRAM, refresh_every=100, tol=TOL,
                                max_iter=20000)
+    from paper_2004_02480_gb300 import autotune
+    tuned = autotune.tune_solve(A, b, p, x_star=xs)       # loop CTA count, untimed
     ev = _events(torch, 5)
     csk.set_stage_events(p, ev)
     csk.csk_solve(A, b, p, x_star=xs)                     # warm-up

@@ -62,7 +62,7 @@ def tune_solve(A: torch.Tensor, b: torch.Tensor, params: csk.csk_params, x_star=
         best = None
         variants = (1, 2) if params.path == csk.GEMV and A.dtype == torch.float32 else (0,)
         for variant in variants:
-            for grid in candidates(sms):
+            for grid in [0] + candidates(sms):               # 0: the library's own plan
                 p = csk.csk_params_default(d=params.d, seed=params.seed, path=params.path,
                                            refresh_every=params.refresh_every, tol=0.0,
                                            max_iter=steps, grid=grid, gemv_variant=variant)
