@@ -218,6 +218,8 @@ def run_c1(args):
     s = synth.gaussian_system(2000, 50, 0, np.float64)
     A, b, xs = (torch.from_numpy(v).to(dev) for v in (s.A, s.b, s.x_star))
     p = csk.csk_params_default(d=500, seed=0, tol=TOL)
+    from paper_2004_02480_gb300 import autotune
+    autotune.tune_solve(A, b, p, x_star=xs)               # loop CTA count, untimed
     ws = csk._workspace(csk.csk_solve_workspace_size(2000, 50, csk.CSK_F64, p), dev)
     x = torch.empty(50, dtype=torch.float64, device=dev)
     info = torch.zeros(64, dtype=torch.uint8, device=dev)

@@ -41,9 +41,15 @@ def _store(cache):
     os.replace(tmp, CACHE)
 
 
-def candidates(sms: int):
+def candidates(sms: int, rows: int | None = None):
+    """CTA counts to time: fractions of the SM count, and for problems small
+    enough that a few dozen CTAs hold all rows (a cheaper exchange), the
+    counts 8..64 that leave at least 4 rows per CTA."""
     fr = [1.0, 0.9, 0.84, 0.75, 0.66, 0.6, 0.5]
-    return sorted({max(1, int(round(sms * f))) for f in fr}, reverse=True)
+    out = {max(1, int(round(sms * f))) for f in fr}
+    if rows is not None:
+        out |= {g for g in (8, 12, 16, 24, 32, 40, 48, 64) if g <= sms and 4 * g <= rows}
+    return sorted(out, reverse=True)
 
 
 def tune_solve(A: torch.Tensor, b: torch.Tensor, params: csk.csk_params, x_star=None,
@@ -62,7 +68,7 @@ def tune_solve(A: torch.Tensor, b: torch.Tensor, params: csk.csk_params, x_star=
         best = None
         variants = (1, 2) if params.path == csk.GEMV and A.dtype == torch.float32 else (0,)
         for variant in variants:
-            for grid in [0] + candidates(sms):               # 0: the library's own plan
+            for grid in [0] + candidates(sms, rows):         # 0: the library's own plan
                 p = csk.csk_params_default(d=params.d, seed=params.seed, path=params.path,
                                            refresh_every=params.refresh_every, tol=0.0,
                                            max_iter=steps, grid=grid, gemv_variant=variant)
