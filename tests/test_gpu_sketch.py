@@ -108,6 +108,22 @@ def test_sketch_fp64_bit_exact(csk, m, n, d):
     assert np.array_equal(s.bt.cpu().numpy(), bt)
 
 
+@pytest.mark.parametrize("m,n,d,R", [(3000, 40, 300, 1), (3000, 40, 300, 3), (5000, 130, 60, 1),
+                                     (999, 7, 2000, 1)])
+def test_sketch_fp64_rhs_bit_exact(csk, m, n, d, R):
+    """FP64 right-hand sides: one column (8 buckets per warp, lane g summing
+    bucket g's rows in order) and several (a warp per bucket), including
+    buckets of hundreds of rows (d = 60) and many empty ones (d > m)."""
+    rng = np.random.default_rng(7 * m + R)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal((m, R)) if R > 1 else rng.standard_normal(m)
+    s = _gpu_sketch(csk, A, b, d, 11)
+    h, sg = oracle.count_sketch_map(11, m, d)
+    At, bt = oracle.sketch(A, b, h, sg, d)
+    assert np.array_equal(s.At.cpu().numpy(), At)
+    assert np.array_equal(s.bt.cpu().numpy().reshape(bt.shape), bt)
+
+
 def test_sketch_strided_lda(csk):
     rng = np.random.default_rng(0)
     full = rng.standard_normal((3000, 80)).astype(np.float32)
