@@ -608,10 +608,12 @@ template <> struct Chunk<double> {
 };
 
 // Rows per warp per block: a block holds kWarps * RPB rows of at most
-// 32 * CPL chunks (<= 32 KB).
-template <int CPL>
+// 32 * CPL chunks (<= 32 KB).  FP64 rows of up to 32 chunks (64 columns) take
+// 8 rows per warp: the transposed sums and the scoring then serve 8 rows per
+// warp instruction (FP64 instructions cost the same whatever the lanes hold).
+template <typename T, int CPL>
 struct StreamShape {
-    static constexpr int RPB = CPL <= 2 ? 4 : 8 / CPL;
+    static constexpr int RPB = (sizeof(T) == 8 && CPL == 1) ? 8 : (CPL <= 2 ? 4 : 8 / CPL);
     static constexpr int ROWS = kWarps * RPB;
 };
 
@@ -622,7 +624,7 @@ size_t stream_smem_bytes(int R, int n, int esize, int rows_per_blk, int stages) 
 template <typename T, int CPL>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv_stream(IterProblem p, int R, int nst) {
-    constexpr int RPB = StreamShape<CPL>::RPB, SR = StreamShape<CPL>::ROWS;
+    constexpr int RPB = StreamShape<T, CPL>::RPB, SR = StreamShape<T, CPL>::ROWS;
     constexpr int V = Chunk<T>::V;
     using vec = typename Chunk<T>::vec;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -845,12 +847,13 @@ const void* stream_kernel(int dtype, int cpl) {
     }
 }
 
-int stream_rows_per_block(int cpl) {
+int stream_rows_per_block(int dtype, int cpl) {
+    const bool f64 = dtype == CSK_F64;
     switch (cpl) {
-        case 1: return StreamShape<1>::ROWS;
-        case 2: return StreamShape<2>::ROWS;
-        case 4: return StreamShape<4>::ROWS;
-        case 8: return StreamShape<8>::ROWS;
+        case 1: return f64 ? StreamShape<double, 1>::ROWS : StreamShape<float, 1>::ROWS;
+        case 2: return f64 ? StreamShape<double, 2>::ROWS : StreamShape<float, 2>::ROWS;
+        case 4: return f64 ? StreamShape<double, 4>::ROWS : StreamShape<float, 4>::ROWS;
+        case 8: return f64 ? StreamShape<double, 8>::ROWS : StreamShape<float, 8>::ROWS;
         default: return 0;
     }
 }
@@ -1114,9 +1117,9 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
         const int need_c = (n / vlen + 31) / 32;
         const int cpl = need_c <= 1 ? 1 : need_c <= 2 ? 2 : need_c <= 4 ? 4 : need_c <= 8 ? 8 : 0;
         int nst = kMaxStreamStages;
-        while (cpl && nst > 2 && stream_smem_bytes(R, n, s, stream_rows_per_block(cpl), nst) > budget)
+        while (cpl && nst > 2 && stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst) > budget)
             --nst;
-        const size_t sm = cpl ? stream_smem_bytes(R, n, s, stream_rows_per_block(cpl), nst) : 0;
+        const size_t sm = cpl ? stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst) : 0;
         if (cpl && sm <= budget) {
             cfg->stream_cpl = cpl;
             cfg->stream_stages = nst;
