@@ -280,7 +280,7 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
 template <typename T, int NR>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv(IterProblem p, int R, int cache_rows) {
-    extern __shared__ __align__(16) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ RedShared<T> sh;
     int par = 0;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
@@ -863,7 +863,7 @@ int stream_rows_per_block(int dtype, int cpl) {
 // full x in FP64 for the refresh (npad doubles)
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gram(IterProblem p, int R) {
-    extern __shared__ __align__(16) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ RedShared<float> sh;
     int par = 0;
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
