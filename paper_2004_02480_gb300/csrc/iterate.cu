@@ -289,11 +289,16 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     const int r0 = min(d, b * R), r1 = min(d, r0 + R), nr = r1 - r0;
     const int c0 = (int)((int64_t)n * b / G), c1 = (int)((int64_t)n * (b + 1) / G);
     const int npad = (n + 3) & ~3, Rpad = (R + 3) & ~3, spad = ((n + G - 1) / G + 4) & ~3;
+    // FP64 with x*: every CTA keeps all of x* and computes ||x - x*||^2 itself
+    // (one warp, during the exchange's poll), so the FP64 statistic leaves the
+    // CTA reductions and the exchange; FP32 sums its share of the columns
+    constexpr bool kLocalStat = sizeof(T) == 8;
     T* xs = reinterpret_cast<T*>(dsm);
     T* w2s = xs + npad;
     T* bts = w2s + Rpad;
     T* xss = bts + Rpad;
-    T* As = xss + spad;
+    T* As = xss + (kLocalStat ? npad : spad);
+    __shared__ T stat_local;
     const T* At = static_cast<const T*>(p.At);
     const T* bt = static_cast<const T*>(p.bt);
     const T* x0 = static_cast<const T*>(p.x0);
@@ -304,8 +309,12 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
         w2s[q] = weight_of<T>(p.N2[r0 + q]);
         bts[q] = bt[r0 + q];
     }
-    if (xstar)
-        for (int c = c0 + tid; c < c1; c += blockDim.x) xss[c - c0] = xstar[c];
+    if (xstar) {
+        if (kLocalStat)
+            for (int c = tid; c < n; c += blockDim.x) xss[c] = xstar[c];
+        else
+            for (int c = c0 + tid; c < c1; c += blockDim.x) xss[c - c0] = xstar[c];
+    }
     if (cache_rows)
         for (int64_t e = tid; e < (int64_t)nr * n; e += blockDim.x) {
             const int q = (int)(e / n), c = (int)(e - (int64_t)q * n);
@@ -370,19 +379,32 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
                 if (!xstar) c.stat += r * r;
             }
         }
-        if (xstar)
+        if (xstar && !kLocalStat)
             for (int col = c0 + tid; col < c1; col += blockDim.x) {
                 const T t = xs[col] - xss[col - c0];
                 c.stat += t * t;
             }
         c = block_reduce(c, sh, par);    // candidates differ across lanes
+        if (xstar && kLocalStat && warp == kWarps - 1) {
+            // the last warp polls no mailbox while the grid has at most
+            // 32 (kWarps - 1) CTAs: it sums ||x - x*||^2 (columns lane,
+            // lane + 32, ... in order, then the butterfly) meanwhile
+            T acc = T(0);
+            for (int col = lane; col < n; col += 32) {
+                const T t = xs[col] - xss[col];
+                acc = fma(t, t, acc);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) stat_local = acc;
+        }
         // Phase B
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
         }
         ++round;
-        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
+        const T stat = (xstar && kLocalStat) ? stat_local : c.stat;
+        const int dec = decide(stat, threshold, k, p.max_iter, c.key);
         if (dec != INT_MIN) { status = dec; break; }
         if (b == 0 && tid == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
         if (b == 0 && p.x_log && k < p.x_log_len)
@@ -1092,7 +1114,7 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
         cfg->cache_rows = 0;
         cfg->smem = (size_t)(2 * Rpad + 2 * spad) * 4 + (size_t)npad * 8;
     } else {
-        const size_t base = (size_t)(npad + 2 * Rpad + spad) * s;
+        const size_t base = (size_t)(npad + 2 * Rpad + (dtype == CSK_F64 ? npad : spad)) * s;
         const size_t rows = (size_t)R * n * s;
         cfg->cache_rows = (base + rows <= budget) ? 1 : 0;
         cfg->smem = base + (cfg->cache_rows ? rows : 0);
