@@ -361,3 +361,39 @@ def test_gram_matches_library_and_split_error_bound():
     absG = np.abs(A64) @ np.abs(A64).T
     assert np.all(np.abs(Gs - G) <= 2.0 ** -15 * absG)
     assert np.max(np.abs(Gs - G) / absG) > 0           # the split is not exact
+
+
+def test_inconsistent_system_never_beats_least_squares():
+    """Inconsistent b = A x* + e: no iterate reaches a residual below the
+    least-squares residual of the sketched system (numpy lstsq), so the
+    residual stopping rule is met above that floor and never below it.  The
+    oracle's steps remain orthogonal projections onto the chosen rows'
+    hyperplanes: for z on row i_k's hyperplane (here the projection of the
+    least-squares solution onto it), ||x_{k+1} - z||^2 = ||x_k - z||^2 - r^2/N."""
+    m, n, d, seed = 2000, 40, 400, 3
+    s = synth.noisy_system(m, n, seed, 1e-3, np.float64)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, d)
+    xls = np.linalg.lstsq(At, bt, rcond=None)[0]
+    floor = np.sum((bt - At @ xls) ** 2) / np.sum(bt * bt)
+    assert floor > 1e-9                                   # really inconsistent
+    hi = oracle.mwrk(At, bt, tol=10 * floor, max_iter=5000)
+    assert hi.status == 0
+    res_hi = np.sum((bt - At @ hi.x) ** 2) / np.sum(bt * bt)
+    assert floor <= res_hi <= 10 * floor * (1 + 1e-12)
+    lo = oracle.mwrk(At, bt, tol=floor / 10, max_iter=1500, log_len=1501)
+    assert lo.status == 1 and lo.iters == 1500
+    res_lo = np.sum((bt - At @ lo.x) ** 2) / np.sum(bt * bt)
+    assert res_lo >= floor * (1 - 1e-12)
+    # projection identity on step k: z = the projection of x_LS onto row i_k's hyperplane
+    N = np.sum(At * At, axis=1)
+    x = np.zeros(n)
+    for k in range(50):
+        i = lo.ik[k]
+        r = bt[i] - At[i] @ x
+        x1 = x + r / N[i] * At[i]
+        z = xls + (bt[i] - At[i] @ xls) / N[i] * At[i]
+        lhs = np.sum((x1 - z) ** 2)
+        rhs = np.sum((x - z) ** 2) - r * r / N[i]
+        assert abs(lhs - rhs) <= 1e-9 * np.sum((x - z) ** 2)
+        x = x1
