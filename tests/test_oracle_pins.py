@@ -397,3 +397,6 @@ def test_inconsistent_system_never_beats_least_squares():
         rhs = np.sum((x - z) ** 2) - r * r / N[i]
         assert abs(lhs - rhs) <= 1e-9 * np.sum((x - z) ** 2)
         x = x1
+    # and the oracle's own iterate after those 50 steps is this replay
+    r50 = oracle.mwrk(At, bt, tol=0.0, max_iter=50)
+    assert np.allclose(r50.x, x, rtol=1e-12, atol=1e-12 * np.linalg.norm(x))
