@@ -152,10 +152,36 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def oracle_solves(A64, b64, xs, seconds: float, min_solves: int = 1, max_solves: int = 10 ** 9):
-    """Time whole oracle solves of the workload (FP64, all host cores)."""
+def _bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed alone: the measured
+    burst figure, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        if "bf16_tflops" in p:
+            return float(p["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+def gram_work(d, n, bm=128, bn=256, bk=64):
+    """Work of csk_gram on d x n: the tiles it computes (those with an
+    element on or above the diagonal) and their BF16 flops (3 products over
+    the padded K), plus the FP32-equivalent flops of the dense product
+    (2 d^2 n) and of its unique upper triangle (d (d + 1) n)."""
+    dp = (d + bn - 1) // bn * bn
+    kp = (n + bk - 1) // bk * bk
+    nbi, nbj = dp // bm, dp // bn
+    tiles = sum(nbj - (i * bm) // bn for i in range(nbi))
+    return {"tiles": tiles, "bf16_flops": tiles * bm * bn * kp * 2 * 3,
+            "dense_fp32_flops": 2 * d * d * n, "upper_fp32_flops": d * (d + 1) * n}
+
+
+def oracle_solves(A64, b64, xs, seconds: float, min_solves: int = 1, max_solves: int = 10 ** 9,
+                  threads: int | None = None):
+    """Time whole oracle solves of the workload (FP64; all host cores, or
+    `threads` of them -- 1 is the literal single-thread Algorithm 1)."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     n_done, its = 0, []
     while n_done < max_solves and (n_done < min_solves or time.perf_counter() - t0 < seconds):
@@ -349,14 +375,16 @@ def run_precision(args):
     return 0
 
 
-def run_batched(args):
-    """batched form: 256 systems (m log-uniform [5000, 200000], n uniform
-    [50, 1000], d = 10 n) x 64 right-hand sides, one persistent launch replayed
-    from a CUDA graph, against the plain single-system GPU solve."""
-    import torch
-    from paper_2004_02480_gb300 import csk, synth
-    csk.lib()
-    dev = torch.device("cuda", 0)
+def batched_measure(torch, csk, dev, K, warmup, sample=32):
+    """The batched form: 256 systems (m log-uniform [5000, 200000], n uniform
+    [50, 1000], d = 10 n) x 64 right-hand sides, A and X* iid N(0,1) FP32,
+    B = A X*.  The launch shape comes from the batched autotuner (installed as
+    the batch's plan, so the captured call with threads = grid = 0 uses it);
+    the call is captured once in a CUDA graph and replayed K times.  The plain
+    comparator solves a sample of the same (system, right-hand side) pairs one
+    at a time with csk_solve, its loop CTA count and variant autotuned per
+    shape for both residual paths, and takes the faster path per solve."""
+    from paper_2004_02480_gb300 import autotune, synth
     S, R = 256, 64
     shapes = synth.batched_shapes(S, 5000, 200000, 50, 1000, seed=7)
     g = torch.Generator(device=dev).manual_seed(11)
@@ -366,19 +394,8 @@ def run_batched(args):
         X = torch.randn((n, R), generator=g, device=dev, dtype=torch.float32)
         batch.append(csk.BatchSystem(A=A, B=A @ X, d=10 * n, seed=1000 + i, Xstar=X))
     ws = torch.empty(csk.csk_solve_batched_workspace_size(batch), dtype=torch.uint8, device=dev)
-    # CTA size: the faster of two, by one untimed run each
-    best = None
-    for threads in (256, 512):
-        p = csk.csk_params_default(threads=threads)
-        csk.csk_solve_batched(batch, p, ws=ws)
-        e0, e1 = _events(torch, 2)
-        e0.record()
-        csk.csk_solve_batched(batch, p, ws=ws, sync=False)
-        e1.record()
-        torch.cuda.synchronize()
-        if best is None or e0.elapsed_time(e1) < best[1]:
-            best = (threads, e0.elapsed_time(e1))
-    p = csk.csk_params_default(threads=best[0])
+    tuned = autotune.tune_batched(batch, ws=ws, use_cache=False)
+    p = csk.csk_params_default()            # threads = grid = 0: the installed plan
     st = torch.cuda.Stream(dev)
     st.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(st):
@@ -388,10 +405,9 @@ def run_batched(args):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         csk.csk_solve_batched(batch, p, ws=ws, sync=False)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         graph.replay()
     torch.cuda.synchronize()
-    K = max(1, min(args.steps, 10))
     e0, e1 = _events(torch, 2)
     e0.record()
     for _ in range(K):
@@ -401,40 +417,107 @@ def run_batched(args):
     ms = e0.elapsed_time(e1) / K
     recs = [np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=csk.INFO_DTYPE) for y in batch]
     ok = all(int(r["status"].max()) == 0 and float(r["rse"].max()) <= TOL for r in recs)
+    grids = {int(v) for r in recs for v in r["grid"]}
     its = np.concatenate([r["iters"] for r in recs])
     # plain single-system GPU CSK on a sample of the same solves (one RHS each)
-    plain = {}
     rng = np.random.default_rng(3)
-    sample = [(int(i), int(rng.integers(R))) for i in rng.integers(S, size=32)]
-    for name, path in (("gram", csk.GRAM), ("gemv", csk.GEMV)):
-        t_ms, good = [], True
-        for i, r in sample:
-            y = batch[i]
+    pairs = [(int(i), int(rng.integers(R))) for i in rng.integers(S, size=sample)]
+    per_path = {"gram": [], "gemv": []}
+    good = True
+    for i, r in pairs:
+        y = batch[i]
+        b = y.B[:, r].contiguous()
+        xsr = y.Xstar[:, r].contiguous()
+        for name, path in (("gram", csk.GRAM), ("gemv", csk.GEMV)):
             pp = csk.csk_params_default(d=y.d, seed=y.seed, path=path, tol=TOL)
-            b = y.B[:, r].contiguous()
-            xsr = y.Xstar[:, r].contiguous()
+            autotune.tune_solve(y.A, b, pp, x_star=xsr)            # per shape, cached
             csk.csk_solve(y.A, b, pp, x_star=xsr)
             a0, a1 = _events(torch, 2)
             a0.record()
             _, inf = csk.csk_solve(y.A, b, pp, x_star=xsr, sync=False)
             a1.record()
             torch.cuda.synchronize()
-            good &= csk.read_info(inf)["status"] == 0
-            t_ms.append(a0.elapsed_time(a1))
-        plain[name] = {"solves_per_s": 1e3 / float(np.mean(t_ms)), "sampled_solves": len(sample),
-                       "all_converged": bool(good)}
+            rr = csk.read_info(inf)
+            good &= rr["status"] == 0 and rr["rse"] <= TOL
+            per_path[name].append(a0.elapsed_time(a1))
+    best_ms = [min(a, b) for a, b in zip(per_path["gram"], per_path["gemv"])]
+    plain = {"solves_per_s": 1e3 / float(np.mean(best_ms)),
+             "gram_solves_per_s": 1e3 / float(np.mean(per_path["gram"])),
+             "gemv_solves_per_s": 1e3 / float(np.mean(per_path["gemv"])),
+             "sampled_solves": len(pairs), "all_converged": bool(good),
+             "how": "csk_solve per (system, RHS), loop CTA count and variant autotuned per shape "
+                    "(autotune.tune_solve) for the GRAM and GEMV paths, faster path per solve"}
     value = S * R / (ms * 1e-3)
+    return {"solves_per_s": value, "ms_per_launch": ms, "replays": K, "all_converged": bool(ok),
+            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+            "tuned": {"threads": tuned["threads"], "grid": tuned["grid"],
+                      "candidates_ms": tuned.get("timings")},
+            "grid_used": sorted(grids), "plain_single_system": plain,
+            "speedup_over_plain": value / plain["solves_per_s"],
+            "workload": "256 systems, m log-uniform [5000,200000], n uniform [50,1000], d=10n, "
+                        "64 right-hand sides each, FP32, GRAM path, CUDA-graph replay"}
+
+
+def sketch_gram_measure(torch, csk, dev, reps=5):
+    """The precision form's sketch and Gram matrix: A 1e6 x 1000 FP32 =
+    G diag(sigma) Q (kappa 1e3), d = 20000.  Whole csk_sketch call (sort
+    chain, A pass, b pass) and whole csk_gram call (split, tcgen05 product,
+    diagonal), each timed with CUDA events over `reps` calls after a warm-up;
+    A (4 GB) is far larger than L2."""
+    from paper_2004_02480_gb300 import synth
+    m, n, d = 1_000_000, 1000, 20000
+    A, b, _ = synth.conditioned_system_device(m, n, 0, 1e3, dev)
+    sk = csk.csk_sketch(A, d, 0, b)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = _events(torch, 2)
+        e0.record()
+        sk = csk.csk_sketch(A, d, 0, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    sk_ms = float(np.median(ts))
+    del A, b
+    G = csk.csk_gram(sk.At, sk.norms2)
+    tg = []
+    for _ in range(reps):
+        e0, e1 = _events(torch, 2)
+        e0.record()
+        G = csk.csk_gram(sk.At, sk.norms2)
+        e1.record()
+        torch.cuda.synchronize()
+        tg.append(e0.elapsed_time(e1))
+    g_ms = float(np.median(tg))
+    del G
+    hbm, hk = _peaks()
+    bf16, bk = _bf16_peak()
+    w = gram_work(d, n)
+    sk_gbs = sketch_bytes(m, n, d) / (sk_ms * 1e-3) / 1e9
+    issued = w["bf16_flops"] / (g_ms * 1e-3) / 1e12
+    return {"workload": "A 1000000x1000 FP32 (kappa 1e3), d=20000",
+            "sketch_ms": sk_ms, "sketch_gbs": sk_gbs, "sketch_frac_of_" + hk + "_hbm": sk_gbs / hbm,
+            "gram_ms": g_ms,
+            "gram_bf16_issued_tflops": issued, "gram_bf16_frac_of_" + bk + "_peak": issued / bf16,
+            "gram_fp32_equiv_tflops_dense": w["dense_fp32_flops"] / (g_ms * 1e-3) / 1e12,
+            "gram_fp32_equiv_tflops_upper": w["upper_fp32_flops"] / (g_ms * 1e-3) / 1e12,
+            "note": "BF16 issued = computed 128x256 tiles (those touching the upper triangle) x 3 "
+                    "products x padded K; dense = 2 d^2 n, upper = d (d+1) n FP32-equivalent flops"}
+
+
+def run_batched(args):
+    """batched form alone: its own JSON line (solves/s of the graph replay)."""
+    import torch
+    from paper_2004_02480_gb300 import csk
+    csk.lib()
+    dev = torch.device("cuda", 0)
+    r = batched_measure(torch, csk, dev, max(1, min(args.steps, 10)), max(1, args.warmup))
     print(json.dumps({
         "metric": "solves/s at RES<=1e-6, batched form (one persistent launch in a CUDA graph)",
-        "value": value, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1, "steps": K,
-        "warmup": max(1, args.warmup), "ms_per_step": ms, "dtype": "f32",
-        "data": "synthetic (A, X* iid N(0,1), B = A X*)",
-        "config": {"workload": "256 systems, m log-uniform [5000,200000], n uniform [50,1000], "
-                               "d=10n, 64 right-hand sides each, FP32, GRAM path",
-                   "threads": best[0]},
-        "all_converged": bool(ok), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
-        "plain_single_system": plain,
-        "speedup_over_plain_gram": value / plain["gram"]["solves_per_s"]}), flush=True)
+        "value": r["solves_per_s"], "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+        "steps": r["replays"], "warmup": max(1, args.warmup), "ms_per_step": r["ms_per_launch"],
+        "dtype": "f32", "data": "synthetic (A, X* iid N(0,1), B = A X*)",
+        "config": {"workload": r["workload"]}, **{k: v for k, v in r.items() if k != "workload"}}),
+        flush=True)
     return 0
 
 
@@ -464,6 +547,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, sketch/Gram and exchange-floor blocks (all outside "
+                         "the timed steps)")
     ap.add_argument("--grid", type=int, default=0, help="loop CTA count (0 = autotune)")
     ap.add_argument("--variant", type=int, default=0, help="loop variant 1-3 (0 = autotune)")
     ap.add_argument("--workload", default="plain",
@@ -584,6 +670,25 @@ def main():
             "status": mrec[0]["status"], "stream_gbs": m_gbs}
     del wsm
 
+    # latency floor of one step: the same CTA count running only the
+    # exchange (CTA reduction + mailbox round trip), 2000 rounds per launch
+    floor_us = None
+    if not args.no_extras:
+        fl_ws = csk._workspace(csk.lib().csk_exchange_floor_workspace_size(recs[0]["grid"]), dev)
+        fts = []
+        for _ in range(6):
+            f0, f1 = _events(torch, 2)
+            f0.record()
+            csk.csk_exchange_floor(recs[0]["grid"], 2000, device=dev, ws=fl_ws)
+            f1.record()
+            torch.cuda.synchronize()
+            fts.append(f0.elapsed_time(f1))
+        floor_us = 1e3 * float(np.median(fts[1:])) / 2000
+    north = None
+    if world == 1 and not args.no_extras:
+        north = {"batched": batched_measure(torch, csk, dev, 3, 1),
+                 "precision_sketch_gram": sketch_gram_measure(torch, csk, dev)}
+
     from paper_2004_02480_gb300 import replicas
     job = replicas.aggregate(ms * 1e-3, K, launches, ok, device=dev)
     job_e2e = replicas.aggregate(te, E, 0, e2e_ok, device=dev)
@@ -607,13 +712,34 @@ def main():
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        n_done, dt, cores, its = oracle_solves(s.A.astype(np.float64), s.b.astype(np.float64),
-                                               s.x_star, args.cpu_seconds)
+        A64, b64 = s.A.astype(np.float64), s.b.astype(np.float64)
+        n_done, dt, cores, its = oracle_solves(A64, b64, s.x_star, args.cpu_seconds)
+        n1, dt1, _, its1 = oracle_solves(A64, b64, s.x_star, 0.0, 1, 1, threads=1)
         cpu = {"value": n_done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n_done} whole oracle solves of this workload (FP64 sketch + literal "
-                         f"Algorithm 1, mean IT {np.mean(its):.1f}) in {dt:.1f} s"}
+                         f"Algorithm 1 with the residual rows on {cores} OpenMP threads, mean IT "
+                         f"{np.mean(its):.1f}) in {dt:.1f} s",
+               "single_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{n1} whole oracle solve, literal Algorithm 1 on one "
+                                           f"thread (IT {its1[0]}), {dt1:.1f} s"}}
 
     value = job["throughput"]
+    us_step = 1e3 * it_ms / (mean_it + 1)
+    hbm_eq = {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": achieved / hbm,
+              "note": "algorithmic bytes = (IT+1) residual evaluations x (4dn + 4(d+2n)); At stays "
+                      "on chip, so this is not DRAM traffic (see traffic)"}
+    if tuned["gemv_variant"] == 3 or floor_us is None:
+        roofline = {"kernel": loop_kernel, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                    "traffic": traffic}
+    else:
+        # the loop keeps At on chip; a step is bound by the inter-CTA exchange
+        roofline = {"kernel": loop_kernel, "bound": "latency", "achieved": 1e6 / us_step,
+                    "peak": 1e6 / floor_us, "unit": "steps/s", "frac": floor_us / us_step,
+                    "peak_kind": "measured: csk_exchange_floor on the same CTA count (the step's "
+                                 "CTA reduction + mailbox round trip with no arithmetic)",
+                    "us_per_step": us_step, "floor_us_per_step": floor_us,
+                    "traffic": traffic, "hbm_equivalent": hbm_eq}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -628,13 +754,7 @@ def main():
                       "iters_mean": mean_it, "rse_max": max(r["rse"] for r in recs),
                       "grid": recs[0]["grid"],
                       "sketch_gbs": sk_gbs, "sketch_frac_of_" + peak_kind + "_hbm": sk_gbs / hbm},
-        "roofline": {"kernel": loop_kernel,
-                     "bound": "hbm", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "traffic": traffic,
-                     "note": "algorithmic bytes = (IT+1) residual evaluations x (4dn + 4(d+2n)); "
-                             "At stays on chip (registers or shared memory), so this is not DRAM "
-                             "traffic; the loop is bound by the per-step exchange latency"},
+        "roofline": roofline,
         "e2e": {"value": job_e2e["throughput"], "unit": UNIT,
                 "h2d_bytes_per_step": int(s.A.nbytes + s.b.nbytes + 4 * N_COLS),
                 "d2h_bytes_per_step": int(4 * N_COLS + 64), "valid": bool(e2e_ok),
@@ -649,6 +769,7 @@ def main():
                        "csk_ms": ms / K, "csk_speedup_over_mwrk": mwrk["ms"] / (ms / K),
                        "note": "MWRK (d = 0, Remark 1) on the same A, b on the GPU, median of 3 "
                                "solves; not part of the timed steps"},
+        "north_star": north,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -99,6 +99,11 @@ typedef struct {
                                the sketch, [1] after sketch and row norms, [2]
                                before the iteration (after the Gram matrix),
                                [3] after the iteration, [4] after the check     */
+    int32_t log_system;     /* csk_solve_batched: ik_log / x_log record the
+                               (system log_system, right-hand side log_rhs)
+                               pair -- indices into the caller's array and
+                               the system's columns; ignored by csk_solve   */
+    int32_t log_rhs;
 } csk_params;
 
 /* Outcome of one solve, written by the device (64 bytes). */
@@ -130,6 +135,55 @@ int csk_version(void);
  * (all devices and threads).  Lets a caller count the library's launches in
  * a region by differencing two reads. */
 int64_t csk_kernel_launches(void);
+
+/* ----------------------------------------------------------------------
+ * csk_info_sync -- read a solve's outcome on the host.
+ *
+ * Algorithm 1's OUTPUT is x; its outcome under the Section 3 stopping rule
+ * (converged at RES <= tol, step cap, failure) and IT are written by the
+ * device into a csk_info record when the stream reaches the end of the
+ * solve.  This copies the record info_dev (device, 64 bytes) into info_host
+ * (host memory; page-locked or pageable) after the work queued on `stream`
+ * so far, waits for the stream, and returns info_host->status (a csk_status:
+ * CSK_OK, CSK_MAXITER, CSK_ENUMERIC, CSK_ETIMEOUT, ...).  Returns CSK_EINVAL
+ * for a NULL pointer and CSK_ECUDA if the copy or the wait fails (the host
+ * record is then unspecified).
+ * -------------------------------------------------------------------- */
+int csk_info_sync(const csk_info *info_dev, csk_info *info_host, void *stream);
+
+/* ----------------------------------------------------------------------
+ * csk_workspace_size -- one workspace size for every device entry point on
+ * a problem of this shape.
+ *
+ * Algorithm 1's INPUT is A (m x n), b (here nrhs right-hand sides), the
+ * sketch size d and x0; the residual path `resid` (csk_resid) selects
+ * how r is updated.  Returns the largest of the workspaces that
+ * csk_sketch(m, d), csk_solve(m, n, dtype, {d, resid}) and -- for FP32 with
+ * d >= 1 and nrhs >= 1 -- csk_solve_batched of the one system (m, n, d,
+ * nrhs) need, so a caller can size one buffer up front.  0 for invalid
+ * sizes (m, n < 1, d < 0, nrhs < 0, bad dtype or path).
+ * -------------------------------------------------------------------- */
+size_t csk_workspace_size(int64_t m, int64_t n, int64_t d, int32_t nrhs, int32_t dtype,
+                          int32_t resid);
+
+/* ----------------------------------------------------------------------
+ * csk_exchange_floor -- the latency floor of one step of the persistent
+ * loop (no counterpart in the paper: a measurement aid).
+ *
+ * Every step of csk_solve's single-system loop ends with one exchange among
+ * its CTAs: each CTA reduces its candidate for i_k across its warps, then
+ * publishes it to every other CTA and waits for all of theirs.  This
+ * enqueues one cooperative launch of `grid` CTAs (1 <= grid <= 320) that
+ * runs `rounds` such exchanges (CTA reduction + mailbox round trip) and
+ * nothing else, so (event time) / rounds is the per-step time of the loop
+ * with its arithmetic taken away -- the floor a step cannot go below with
+ * this exchange.  ws: csk_exchange_floor_workspace_size(grid) bytes (the
+ * mailboxes and a status record).  Returns CSK_EINVAL for bad arguments,
+ * CSK_ECUDA if the launch fails.
+ * -------------------------------------------------------------------- */
+size_t csk_exchange_floor_workspace_size(int32_t grid);
+
+int csk_exchange_floor(int32_t grid, int64_t rounds, void *ws, size_t ws_bytes, void *stream);
 
 /* ----------------------------------------------------------------------
  * csk_sketch -- Algorithm 1, "Initialize": At = S A and Bt = S B.
@@ -171,7 +225,11 @@ int csk_sketch(const void *A, int64_t m, int64_t n, int64_t lda,
  * CSK_ENOMEM before anything is enqueued.
  * The first call on a device looks up the array's device address for that
  * device (a one-time host-side set-up); make that first call before any
- * stream capture.  Every call shares the one array (it keeps the last
+ * stream capture.  The address is kept for the life of the process, so the
+ * entry point must not be used on a device after cudaDeviceReset (a lookup
+ * that failed is not kept: the next call tries again).  The stream must
+ * belong to the current device (CSK_EINVAL otherwise, nothing enqueued).
+ * Every call shares the one array (it keeps the last
  * call's contents; what must start at zero is cleared by each call), so
  * calls whose GPU work overlaps -- on different streams, or from different
  * host threads -- race and give wrong results.  Serialise them.
@@ -248,8 +306,8 @@ int csk_solve_host(const void *A_host, int64_t m, int64_t n, int64_t lda,
 /* ----------------------------------------------------------------------
  * csk_solve_host_many -- a sequence of csk_solve_host problems, solved one
  * after another on `stream`, with the host-to-device copies of problem k+1
- * (on a stream the call creates and destroys) overlapping the solve of
- * problem k.  Every problem is an independent run of Algorithm 1 with the
+ * (on a copy stream the library creates once per device, with its events,
+ * and reuses in later calls) overlapping the solve of problem k.  Every problem is an independent run of Algorithm 1 with the
  * same params (one sketch seed, d, tolerance, path); overlapping the copies
  * changes no arithmetic.  This is the pipelining a solver service applies
  * to a stream of systems arriving in host memory (the paper has no
@@ -297,7 +355,11 @@ int csk_solve_host_many(const csk_host_problem *probs, int32_t count, int32_t dt
  * info: nrhs csk_info records per system (device), written when the pair
  * finishes; rse is FP64, resid uses a compensated FP32 dot product.
  * params: tol, max_iter, refresh_every (FP64 residual recomputation period,
- * 0 = never), grid and threads (0 = library choice); d/seed/path ignored.
+ * 0 = never), grid and threads; d/seed/path ignored.  With threads = grid = 0
+ * the call uses the launch shape installed for this batch's signature by
+ * csk_solve_batched_set_plan (an autotuner's pick), else the library's
+ * default (256 threads, as many CTAs as stay resident).  ik_log / x_log (with
+ * log_system, log_rhs) record i_k and x_k of one pair, as in csk_solve.
  * The host array `sys` is read during the call only, and nothing in the call
  * synchronises, so the sequence can be captured in a CUDA graph.
  * ws: csk_solve_batched_workspace_size(sys, nsys) bytes (sketches, Gram
@@ -322,6 +384,20 @@ size_t csk_solve_batched_workspace_size(const csk_system *sys, int32_t nsys);
 
 int csk_solve_batched(const csk_system *sys, int32_t nsys, const csk_params *params,
                       void *ws, size_t ws_bytes, void *stream);
+
+/* Install the launch shape (threads per CTA: 64..512, a multiple of 32; CTAs
+ * >= 1) that csk_solve_batched uses for batches of this signature when called
+ * with threads = grid = 0, on the current device; threads = grid = 0 removes
+ * it.  The signature (csk_solve_batched_signature) is the number of
+ * right-hand sides per (floor(log2 d), floor(log2 n)) bin, so batches with
+ * the same shape distribution share a plan.  An autotuner times candidate
+ * shapes with explicit threads / grid and installs the fastest; the shape
+ * changes only how pairs are scheduled, not any pair's arithmetic at a given
+ * thread count.  Host-only (the table lives in the process); thread-safe.
+ * Returns CSK_EINVAL for bad arguments. */
+int csk_solve_batched_set_plan(const csk_system *sys, int32_t nsys, int32_t threads,
+                               int32_t grid);
+uint64_t csk_solve_batched_signature(const csk_system *sys, int32_t nsys);
 
 /* ----------------------------------------------------------------------
  * csk_synth_systems -- seeded Gaussian test systems generated on the device

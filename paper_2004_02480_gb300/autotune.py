@@ -1,10 +1,22 @@
-"""Autotuner for the persistent MWRK loop: picks the CTA count (grid) and the
-GEMV variant (rows of the sketch in shared memory or in registers) by timing
-a fixed number of steps on the caller's own problem, and caches the choice
-in a JSON file keyed by (rows, n, dtype, path, SM count).
+"""Autotuners of the two persistent launches.
 
-Each candidate runs the loop for `steps` steps with tol = 0 (so every
-candidate does the same work), timed with CUDA events around the loop only.
+Single system (:func:`tune_solve`): picks the CTA count (grid) and the GEMV
+variant (rows of the sketch in shared memory or in registers) by timing a
+fixed number of steps on the caller's own problem, and caches the choice in a
+JSON file keyed by (rows, n, dtype, path, SM count).  Each candidate runs the
+loop for `steps` steps with tol = 0 (so every candidate does the same work),
+timed with CUDA events around the loop only.
+
+Batched (:func:`tune_batched`): picks the threads per CTA and the CTAs per SM
+of csk_solve_batched's persistent launch by timing whole calls on the
+caller's batch, then installs the winner in the library
+(csk_solve_batched_set_plan) under the batch's signature -- the histogram of
+right-hand sides over (log2 d, log2 n) bins -- so later calls with
+threads = grid = 0, graph captures included, use it.  The residual path is
+not a candidate: the batched launch always takes the GRAM update, whose step
+reads one row of G_s (d values) where the GEMV update reads all of At_s
+(d n values), and G_s costs one tensor-core product shared by the system's
+right-hand sides.
 """
 from __future__ import annotations
 
@@ -95,4 +107,83 @@ def tune_solve(A: torch.Tensor, b: torch.Tensor, params: csk.csk_params, x_star=
                 _store(cache)
     params.grid = best["grid"]
     params.gemv_variant = best["gemv_variant"]
+    return dict(best)
+
+
+# threads per CTA of the batched loop, and the limits that bound its CTAs per
+# SM: 128 registers a thread (its launch bound), 64K registers and 228 KB of
+# shared memory per SM, the kernel's static shared memory
+BATCH_THREADS = (128, 256, 384, 512)
+_REGS_PER_THREAD, _REGS_PER_SM, _SMEM_PER_SM, _SMEM_STATIC = 128, 65536, 233472, 2048
+
+
+def batched_smem_bytes(dmax: int, nmax: int) -> int:
+    """Dynamic shared memory of a batched CTA: r and the row weights (d each)
+    and x and x* (n each), FP32, padded to 4."""
+    return (2 * ((dmax + 3) // 4 * 4) + 2 * ((nmax + 3) // 4 * 4)) * 4
+
+
+def batched_candidates(sms: int, dmax: int, nmax: int, max_per_sm: int = 4):
+    """(threads, grid) launch shapes to time: every thread count of
+    BATCH_THREADS with 1 .. k CTAs per SM, k the most that registers and
+    shared memory let stay resident (more would only queue)."""
+    smem = batched_smem_bytes(dmax, nmax) + _SMEM_STATIC
+    out = []
+    for t in BATCH_THREADS:
+        by_regs = _REGS_PER_SM // (_REGS_PER_THREAD * t)
+        by_smem = _SMEM_PER_SM // smem
+        k = min(max_per_sm, by_regs, by_smem)
+        out += [(t, per * sms) for per in range(1, k + 1)]
+    return out
+
+
+def _batch_key(sig: int, sms: int) -> str:
+    return f"batched:sig={sig}:sms={sms}"
+
+
+def tune_batched(batch, ws=None, params=None, reps: int = 1, use_cache: bool = True) -> dict:
+    """Time csk_solve_batched on ``batch`` for every candidate shape and
+    install the fastest as the batch signature's plan; returns {threads,
+    grid, ms, timings}.  Calls are synchronous and not captured (tuning runs
+    before any graph capture)."""
+    dev = batch[0].A.device
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    dmax = max(y.d for y in batch)
+    nmax = max(y.A.shape[1] for y in batch)
+    sig = csk.csk_solve_batched_signature(batch)
+    key = _batch_key(sig, sms)
+    with _lock:
+        cache = _load() if use_cache else {}
+    if key in cache:
+        best = cache[key]
+    else:
+        if ws is None:
+            ws = torch.empty(csk.csk_solve_batched_workspace_size(batch), dtype=torch.uint8,
+                             device=dev)
+        base = params if params is not None else csk.csk_params_default()
+        timings = {}
+        best = None
+        for t, g in batched_candidates(sms, dmax, nmax):
+            p = csk.csk_params_default(tol=base.tol, max_iter=base.max_iter,
+                                       refresh_every=base.refresh_every, threads=t, grid=g)
+            csk.csk_solve_batched(batch, p, ws=ws, sync=False)          # warm-up
+            ts = []
+            for _ in range(max(1, reps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                csk.csk_solve_batched(batch, p, ws=ws, sync=False)
+                e1.record()
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            ms = sorted(ts)[len(ts) // 2]
+            timings[f"{t}x{g}"] = ms
+            if best is None or ms < best["ms"]:
+                best = {"threads": t, "grid": g, "ms": ms}
+        best["timings"] = timings
+        if use_cache:
+            with _lock:
+                cache = _load()
+                cache[key] = best
+                _store(cache)
+    csk.csk_solve_batched_set_plan(batch, best["threads"], best["grid"])
     return dict(best)

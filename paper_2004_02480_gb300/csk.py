@@ -45,7 +45,8 @@ class csk_params(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
                 ("x_log", ctypes.c_void_p), ("x_log_len", ctypes.c_int64),
                 ("threads", ctypes.c_int32), ("gemv_variant", ctypes.c_int32),
-                ("stage_events", ctypes.c_void_p * 5)]
+                ("stage_events", ctypes.c_void_p * 5), ("log_system", ctypes.c_int32),
+                ("log_rhs", ctypes.c_int32)]
 
 
 class csk_system(ctypes.Structure):
@@ -126,6 +127,18 @@ def lib():
         L.csk_solve_host_many.restype = ctypes.c_int
         L.csk_synth_systems.argtypes = [ctypes.POINTER(csk_synth_system), i32, P]
         L.csk_synth_systems.restype = ctypes.c_int
+        L.csk_solve_batched_set_plan.argtypes = [ctypes.POINTER(csk_system), i32, i32, i32]
+        L.csk_solve_batched_set_plan.restype = ctypes.c_int
+        L.csk_solve_batched_signature.argtypes = [ctypes.POINTER(csk_system), i32]
+        L.csk_solve_batched_signature.restype = ctypes.c_uint64
+        L.csk_info_sync.argtypes = [P, P, P]
+        L.csk_info_sync.restype = ctypes.c_int
+        L.csk_workspace_size.argtypes = [i64, i64, i64, i32, i32, i32]
+        L.csk_workspace_size.restype = sz
+        L.csk_exchange_floor_workspace_size.argtypes = [i32]
+        L.csk_exchange_floor_workspace_size.restype = sz
+        L.csk_exchange_floor.argtypes = [i32, i64, P, sz, P]
+        L.csk_exchange_floor.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -283,6 +296,37 @@ def read_info(info: torch.Tensor) -> dict:
     """Decode a csk_info record (64 bytes of device memory) on the host."""
     rec = np.frombuffer(info.cpu().numpy().tobytes(), dtype=INFO_DTYPE)[0]
     return {k: rec[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}
+
+
+def csk_info_sync(info: torch.Tensor) -> dict:
+    """Copy a device csk_info record to the host through csk_info_sync (after
+    the work queued on the current stream) and decode it."""
+    dev = _check_cuda(info)
+    host = np.zeros(1, INFO_DTYPE)
+    rc = lib().csk_info_sync(_ptr(info), ctypes.c_void_p(host.ctypes.data), _stream(dev))
+    if rc in (CSK_EINVAL, CSK_ECUDA):          # the call failed (no solve ends so)
+        raise CskError(rc, "csk_info_sync")
+    return info_dict(host)
+
+
+def csk_workspace_size(m: int, n: int, d: int, nrhs: int, dtype: int, resid: int) -> int:
+    """Bytes of one workspace that serves csk_sketch, csk_solve and (FP32)
+    csk_solve_batched on a problem of this shape."""
+    return int(lib().csk_workspace_size(m, n, d, nrhs, dtype, resid))
+
+
+def csk_exchange_floor(grid: int, rounds: int, device=None, ws: torch.Tensor | None = None) -> None:
+    """Enqueue the exchange-only loop (``rounds`` rounds on ``grid`` CTAs) on
+    the current stream; time it with events around the call."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    need = int(lib().csk_exchange_floor_workspace_size(grid))
+    if need == 0:
+        raise CskError(CSK_EINVAL, "csk_exchange_floor_workspace_size")
+    if ws is None:
+        ws = _workspace(need, dev)
+    rc = lib().csk_exchange_floor(grid, rounds, _ptr(ws), ws.numel(), _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_exchange_floor")
 
 
 def csk_solve(A: torch.Tensor, b: torch.Tensor, params: csk_params, x0=None, x_star=None, *,
@@ -532,3 +576,28 @@ def csk_solve_batched(batch: list[BatchSystem], params: csk_params, *, ws: torch
         out.append((y.Xout, [{k: r[k].item() for k in INFO_DTYPE.names if not k.startswith("reserved")}
                              for r in recs]))
     return out
+
+
+def csk_solve_batched_set_plan(batch: list[BatchSystem], threads: int, grid: int) -> None:
+    """Install (threads, grid) as the launch shape csk_solve_batched uses for
+    batches with this batch's signature when called with threads = grid = 0
+    (threads = grid = 0 removes it)."""
+    arr = _systems(batch)
+    rc = lib().csk_solve_batched_set_plan(arr, len(batch), threads, grid)
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_solve_batched_set_plan")
+
+
+def csk_solve_batched_signature(batch: list) -> int:
+    """The batch signature the tuned plans are keyed by.  Accepts BatchSystem
+    objects or plain (m, n, d, nrhs) tuples (no device memory needed)."""
+    arr = (csk_system * len(batch))()
+    for i, y in enumerate(batch):
+        if isinstance(y, BatchSystem):
+            m, n = y.A.shape
+            arr[i] = csk_system(None, m, n, n, None, y.B.shape[1], y.B.shape[1], 0, y.d, 0, None,
+                                None, None, None)
+        else:
+            m, n, d, R = y
+            arr[i] = csk_system(None, m, n, n, None, R, R, 0, d, 0, None, None, None, None)
+    return int(lib().csk_solve_batched_signature(arr, len(batch)))

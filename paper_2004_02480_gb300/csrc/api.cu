@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -60,20 +61,6 @@ void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLay
     L->G = o;     o += path == CSK_RESID_GRAM ? align256((size_t)rows * gram_ld((int)rows) * 4) : 0;
     L->gscr = o;  o += path == CSK_RESID_GRAM ? align256(gram_scratch_bytes((int)rows, (int)n)) : 0;
     L->total = o;
-}
-
-int check_stream_device(cudaStream_t st) {
-    int cur = 0;
-    if (cudaGetDevice(&cur) != cudaSuccess) return CSK_ECUDA;
-    if (st == nullptr) return CSK_OK;
-    // A stream being captured into a CUDA graph cannot be queried for its
-    // device (the query would invalidate the capture); skip the check then.
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return CSK_EINVAL;
-    if (cap != cudaStreamCaptureStatusNone) return CSK_OK;
-    int sd = -1;
-    if (cudaStreamGetDevice(st, &sd) != cudaSuccess) return CSK_EINVAL;
-    return sd == cur ? CSK_OK : CSK_EINVAL;
 }
 
 // AUTO: GEMV while the sketch fits on chip across the SMs (shared memory or
@@ -218,9 +205,76 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     record(params, 4, st);
     return CSK_OK;
 }
+// Copy stream and events of csk_solve_host_many, created once per device and
+// reused: an idle set is taken at the start of a call and returned at its end
+// (calls running at the same time on one device each get a set of their own).
+struct CopyRes {
+    int dev = -1;
+    cudaStream_t cp = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t freed[2] = {nullptr, nullptr};
+};
+std::mutex g_res_mu;
+std::vector<CopyRes> g_res_idle;
+
+void destroy_copy_res(CopyRes& r) {
+    for (int i = 0; i < 2; ++i) {
+        if (r.copied[i]) cudaEventDestroy(r.copied[i]);
+        if (r.freed[i]) cudaEventDestroy(r.freed[i]);
+    }
+    if (r.cp) cudaStreamDestroy(r.cp);
+}
+
+cudaError_t acquire_copy_res(CopyRes* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        for (size_t i = 0; i < g_res_idle.size(); ++i)
+            if (g_res_idle[i].dev == dev) {
+                *out = g_res_idle[i];
+                g_res_idle.erase(g_res_idle.begin() + (std::ptrdiff_t)i);
+                return cudaSuccess;
+            }
+    }
+    CopyRes r;
+    r.dev = dev;
+    e = cudaStreamCreateWithFlags(&r.cp, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&r.copied[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.freed[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        destroy_copy_res(r);
+        return e;
+    }
+    *out = r;
+    return cudaSuccess;
+}
+
+void release_copy_res(const CopyRes& r) {
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    g_res_idle.push_back(r);
+}
 }  // namespace
 
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int check_stream_device(cudaStream_t st) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return CSK_ECUDA;
+    if (st == nullptr) return CSK_OK;
+    // A stream being captured into a CUDA graph cannot be queried for its
+    // device (the query would invalidate the capture); skip the check then.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return CSK_EINVAL;
+    if (cap != cudaStreamCaptureStatusNone) return CSK_OK;
+    int sd = -1;
+    if (cudaStreamGetDevice(st, &sd) != cudaSuccess) return CSK_EINVAL;
+    return sd == cur ? CSK_OK : CSK_EINVAL;
+}
+
 
 namespace {
 std::mutex g_attr_mu;
@@ -296,7 +350,7 @@ const char* csk_strerror(int status) {
     }
 }
 
-int csk_version(void) { return 100; }
+int csk_version(void) { return 200; }
 
 int64_t csk_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -360,11 +414,94 @@ int csk_solve_batched(const csk_system* sys, int32_t nsys, const csk_params* par
     if (!(params->tol >= 0.0) || params->max_iter < 0 || params->refresh_every < 0 ||
         params->grid < 0 || params->threads < 0)
         return CSK_EINVAL;
+    if (params->ik_log_len < 0 || (params->ik_log_len > 0 && !params->ik_log)) return CSK_EINVAL;
+    if (params->x_log_len < 0 || (params->x_log_len > 0 && !params->x_log)) return CSK_EINVAL;
+    BatchLog log;
+    if (params->ik_log_len > 0 || params->x_log_len > 0) {
+        if (params->log_system < 0 || params->log_system >= nsys || params->log_rhs < 0 ||
+            params->log_rhs >= sys[params->log_system].nrhs)
+            return CSK_EINVAL;
+        log.system = params->log_system;
+        log.rhs = params->log_rhs;
+        log.ik = params->ik_log_len > 0 ? params->ik_log : nullptr;
+        log.ik_len = params->ik_log_len;
+        log.x = params->x_log_len > 0 ? static_cast<float*>(params->x_log) : nullptr;
+        log.x_len = params->x_log_len;
+    }
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = check_stream_device(st);
     if (rc != CSK_OK) return rc;
-    return launch_batched(sys, nsys, params, ws, ws_bytes, st);
+    return launch_batched(sys, nsys, params, log, ws, ws_bytes, st);
+}
+
+int csk_solve_batched_set_plan(const csk_system* sys, int32_t nsys, int32_t threads,
+                               int32_t grid) {
+    if (!sys || nsys < 1 || threads < 0 || grid < 0) return CSK_EINVAL;
+    if ((threads == 0) != (grid == 0)) return CSK_EINVAL;
+    if (threads != 0 && (threads < 64 || threads > 512 || (threads & 31))) return CSK_EINVAL;
+    for (int32_t s = 0; s < nsys; ++s)
+        if (sys[s].d < 1 || sys[s].n < 1 || sys[s].nrhs < 1) return CSK_EINVAL;
+    return set_batched_plan(sys, nsys, threads, grid);
+}
+
+uint64_t csk_solve_batched_signature(const csk_system* sys, int32_t nsys) {
+    if (!sys || nsys < 1) return 0;
+    return batched_signature(sys, nsys);
+}
+
+int csk_info_sync(const csk_info* info_dev, csk_info* info_host, void* stream) {
+    if (!info_dev || !info_host) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(info_host, info_dev, sizeof(csk_info), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CSK_ECUDA;
+    return info_host->status;
+}
+
+size_t csk_workspace_size(int64_t m, int64_t n, int64_t d, int32_t nrhs, int32_t dtype,
+                          int32_t resid) {
+    if (m < 1 || n < 1 || d < 0 || nrhs < 0) return 0;
+    if (dtype != CSK_F32 && dtype != CSK_F64) return 0;
+    if (resid < CSK_RESID_GEMV || resid > CSK_RESID_AUTO) return 0;
+    csk_params p;
+    csk_params_default(&p);
+    p.d = d;
+    p.path = resid;
+    size_t need = csk_solve_workspace_size(m, n, dtype, &p);
+    if (d >= 1) need = std::max(need, csk_sketch_workspace_size(m, d));
+    if (dtype == CSK_F32 && d >= 1 && nrhs >= 1) {
+        csk_system y;
+        std::memset(&y, 0, sizeof(y));
+        const uintptr_t any = 256;          // the size depends on shapes only
+        y.A = y.B = reinterpret_cast<const void*>(any);
+        y.Xout = reinterpret_cast<void*>(any);
+        y.info = reinterpret_cast<csk_info*>(any);
+        y.m = m; y.n = n; y.lda = n; y.ldb = nrhs; y.nrhs = nrhs; y.d = d;
+        need = std::max(need, batched_workspace_bytes(&y, 1));
+    }
+    return need;
+}
+
+size_t csk_exchange_floor_workspace_size(int32_t grid) {
+    if (grid < 1 || grid > kMaxIterGrid) return 0;
+    return align256(exchange_bytes(grid)) + 256;
+}
+
+int csk_exchange_floor(int32_t grid, int64_t rounds, void* ws, size_t ws_bytes, void* stream) {
+    if (grid < 1 || grid > kMaxIterGrid || rounds < 1 || !ws) return CSK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    if (ws_bytes < csk_exchange_floor_workspace_size(grid)) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    char* w = static_cast<char*>(ws);
+    Slot* slots = reinterpret_cast<Slot*>(w);
+    csk_info* info = reinterpret_cast<csk_info*>(w + align256(exchange_bytes(grid)));
+    if (cudaMemsetAsync(w, 0, align256(exchange_bytes(grid)) + sizeof(csk_info), st) != cudaSuccess)
+        return CSK_ECUDA;
+    return launch_exchange_probe(grid, rounds, slots, info, st) == cudaSuccess ? CSK_OK : CSK_ECUDA;
 }
 
 size_t csk_solve_workspace_size(int64_t m, int64_t n, int32_t dtype, const csk_params* params) {
@@ -470,13 +607,12 @@ int csk_solve_host_many(const csk_host_problem* probs, int32_t count, int32_t dt
 
     // copies of problem k+1 run on `cp` while problem k is solved on `st`;
     // staging area k % 2 is reused once the solve that read it has finished
-    cudaStream_t cp = nullptr;
-    cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
-    cudaError_t e = cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
-    }
+    CopyRes res;
+    cudaError_t e = acquire_copy_res(&res);
+    if (e != cudaSuccess) return CSK_ECUDA;
+    cudaStream_t cp = res.cp;
+    cudaEvent_t* copied = res.copied;
+    cudaEvent_t* freed = res.freed;
     int first_bad = CSK_OK;
     // the copy stream starts after the work already queued on `st`
     if (e == cudaSuccess) e = cudaEventRecord(freed[0], st);
@@ -524,14 +660,10 @@ int csk_solve_host_many(const csk_host_problem* probs, int32_t count, int32_t dt
         solved = k + 1;
     }
     if (e == cudaSuccess && first_bad == CSK_OK && solved == count) e = queue_out(count - 1);
-    // drain both streams before the events and the copy stream go away
+    // drain both streams before the copy stream and events go back to the pool
     const cudaError_t e1 = cudaStreamSynchronize(cp);
     const cudaError_t e2 = cudaStreamSynchronize(st);
-    for (int i = 0; i < 2; ++i) {
-        if (copied[i]) cudaEventDestroy(copied[i]);
-        if (freed[i]) cudaEventDestroy(freed[i]);
-    }
-    if (cp) cudaStreamDestroy(cp);
+    release_copy_res(res);
     if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) return CSK_ECUDA;
     if (first_bad != CSK_OK) return first_bad;
     for (int32_t k = 0; k < count; ++k)

@@ -16,7 +16,10 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -90,8 +93,15 @@ __device__ __forceinline__ uint32_t key_code(float key) {
     return key != key ? 0xFFFFFFFFu : __float_as_uint(key) + 1u;
 }
 
+// Logs of one unit (ik / x NULL for every other unit): i_k of step k and x_k,
+// the iterate step k selects from (n floats per step).
+struct UnitLog {
+    int32_t* ik;  int64_t ik_len;
+    float* x;     int64_t x_len;
+};
+
 __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
-                           int64_t max_iter, int refresh) {
+                           int64_t max_iter, int refresh, const UnitLog& lg) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
     const int d = S.d, n = S.n, R = S.nrhs;
@@ -243,6 +253,10 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
         if (k >= max_iter) { status = CSK_MAXITER; break; }
         if (c.key != c.key || c.key < 0.0f) { status = CSK_ENUMERIC; break; }
         if (c.key == 0.0f) { status = CSK_OK; break; }
+        // xs holds x_k here (the pass applied the previous step's update)
+        if (lg.ik && k < lg.ik_len && tid == 0) lg.ik[k] = c.idx;
+        if (lg.x && k < lg.x_len)
+            for (int col = tid; col < n; col += nt) lg.x[k * n + col] = xs[col];
         idx = c.idx;
         alpha = c.alpha;
         ++k;
@@ -303,7 +317,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
 
 __global__ void __launch_bounds__(512)
 k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int* counter, float tol,
-                  int64_t max_iter, int refresh) {
+                  int64_t max_iter, int refresh, int log_unit, UnitLog lg) {
     extern __shared__ __align__(16) float sm[];
     __shared__ BatchShared sh;
     for (;;) {
@@ -319,7 +333,8 @@ k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int*
             if (table[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
         }
         const BatchSys S = table[lo];
-        solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh);
+        const UnitLog none = {nullptr, 0, nullptr, 0};
+        solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh, u == log_unit ? lg : none);
     }
 }
 
@@ -368,6 +383,53 @@ int batch_layout(const csk_system* sys, int nsys, BatchLayout* L) {
 
 }  // namespace
 
+// ------------------------------------------------------- tuned plans
+// Launch shapes (threads per CTA, CTAs) installed by an autotuner for a
+// batch signature: the histogram of units (right-hand sides) over
+// (floor(log2 d), floor(log2 n)) bins, so batches with the same shape
+// distribution share a plan whatever their order.
+std::mutex g_plan_mu;
+std::map<std::pair<int, uint64_t>, std::pair<int, int>> g_plans;   // (device, signature)
+
+uint64_t batch_signature(const csk_system* sys, int nsys) {
+    std::map<std::pair<int, int>, int64_t> hist;
+    auto lg = [](int64_t v) { int b = 0; while (v > 1) { v >>= 1; ++b; } return b; };
+    for (int s = 0; s < nsys; ++s) hist[{lg(sys[s].d), lg(sys[s].n)}] += sys[s].nrhs;
+    uint64_t h = 1469598103934665603ull;               // FNV-1a over the sorted bins
+    auto mix = [&h](uint64_t v) {
+        for (int i = 0; i < 8; ++i) { h ^= (v >> (8 * i)) & 0xFF; h *= 1099511628211ull; }
+    };
+    for (const auto& e : hist) {
+        mix((uint64_t)e.first.first);
+        mix((uint64_t)e.first.second);
+        mix((uint64_t)e.second);
+    }
+    return h;
+}
+
+bool lookup_plan(const csk_system* sys, int nsys, int* threads, int* grid) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find({dev, batch_signature(sys, nsys)});
+    if (it == g_plans.end()) return false;
+    *threads = it->second.first;
+    *grid = it->second.second;
+    return true;
+}
+
+int set_batched_plan(const csk_system* sys, int nsys, int threads, int grid) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CSK_ECUDA;
+    const uint64_t key = batch_signature(sys, nsys);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (threads == 0 && grid == 0) g_plans.erase({dev, key});
+    else g_plans[{dev, key}] = {threads, grid};
+    return CSK_OK;
+}
+
+uint64_t batched_signature(const csk_system* sys, int nsys) { return batch_signature(sys, nsys); }
+
 size_t batched_workspace_bytes(const csk_system* sys, int nsys) {
     BatchLayout L;
     if (!sys || nsys < 1 || batch_layout(sys, nsys, &L) != CSK_OK) return 0;
@@ -395,21 +457,23 @@ int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int*
     return CSK_OK;
 }
 
-int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* ws, size_t ws_bytes,
-                   cudaStream_t st) {
+int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
+                   void* ws, size_t ws_bytes, cudaStream_t st) {
     BatchLayout L;
     int rc = batch_layout(sys, nsys, &L);
     if (rc != CSK_OK) return rc;
     if (ws_bytes < L.total) return CSK_EINVAL;
     int threads = 0, grid = 0;
     size_t smem = 0;
-    rc = plan_batched(L.dmax, L.nmax, p->threads, p->grid, &threads, &grid, &smem);
+    int t_req = p->threads, g_req = p->grid;
+    if (t_req == 0 && g_req == 0) (void)lookup_plan(sys, nsys, &t_req, &g_req);   // tuned shape
+    rc = plan_batched(L.dmax, L.nmax, t_req, g_req, &threads, &grid, &smem);
     if (rc != CSK_OK) return rc;
     char* w = static_cast<char*>(ws);
     SortScratch s;
     carve_sort_scratch(w + L.sort, L.mmax, L.dmax, &s);
     std::vector<BatchSys> table(nsys);
-    int units = 0;
+    int units = 0, log_unit = -1;
     for (int q = 0; q < nsys; ++q) {
         const int i = L.order[q];
         const csk_system& y = sys[i];
@@ -432,6 +496,7 @@ int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* w
         e.info = y.info;
         e.ldg = gram_ld((int)y.d);
         e.d = (int)y.d; e.n = (int)y.n; e.nrhs = y.nrhs; e.unit_begin = units;
+        if (i == log.system) log_unit = units + log.rhs;
         units += y.nrhs;
     }
     BatchSys* dtable = reinterpret_cast<BatchSys*>(w + L.table);
@@ -445,8 +510,9 @@ int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* w
     }
     int* counter = reinterpret_cast<int*>(w + L.counter);
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return CSK_ECUDA;
+    const UnitLog lg = {log.ik, log.ik_len, log.x, log.x_len};
     k_iterate_batched<<<grid, threads, smem, st>>>(dtable, nsys, units, counter, (float)p->tol,
-                                                   p->max_iter, p->refresh_every);
+                                                   p->max_iter, p->refresh_every, log_unit, lg);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CSK_OK : CSK_ECUDA;
 }

@@ -997,6 +997,30 @@ k_iterate_gram(IterProblem p, int R) {
     finish(p.info, status, k);
 }
 
+// ------------------------------------------------ exchange floor probe
+// `rounds` rounds of the register loop's per-step exchange -- the CTA
+// reduction of a candidate, then the mailbox round trip with its reduction
+// of the gathered candidates -- and no residual arithmetic.  The candidates
+// are a cheap function of (CTA, thread, round), so the reductions do the
+// same work as in a solve.
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_exchange_probe(Slot* slots, int64_t rounds, csk_info* info) {
+    __shared__ RedShared<float> sh;
+    int par = 0;
+    uint32_t round = 0;
+    const uint32_t me = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t k = 0; k < rounds; ++k) {
+        Red<float> c;
+        c.key = (float)((me * 2654435761u + (uint32_t)k * 40503u) >> 16);
+        c.alpha = 1.0f;
+        c.stat = 1.0f;
+        c.idx = (int32_t)me;
+        c = block_reduce(c, sh, par);
+        if (!exchange(slots, round, c, kDefaultSpin, 0, info, sh, par)) break;
+        ++round;
+    }
+}
+
 // --------------------------------------------------------- final check
 constexpr int kFinalThreads = 128;
 constexpr int kFinalRows = 8;      // rows a warp sums at once in the final check
@@ -1181,6 +1205,21 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
                                     stream ? args_stream
                                            : (path == CSK_RESID_GRAM || reg) ? args_gram : args_gemv,
                                     cfg.smem, st);
+    if (e == cudaSuccess) note_launches(1);
+    return e;
+}
+
+cudaError_t launch_exchange_probe(int grid, int64_t rounds, Slot* slots, csk_info* info,
+                                  cudaStream_t st) {
+    const void* fn = (const void*)k_exchange_probe;
+    int per_sm = 0;
+    cudaError_t e = cached_occupancy(fn, kIterThreads, 0, &per_sm);
+    if (e != cudaSuccess) return e;
+    DevInfo di;
+    if (dev_info(&di) != 0) return cudaErrorUnknown;
+    if ((int64_t)per_sm * di.sms < grid) return cudaErrorCooperativeLaunchTooLarge;
+    void* args[] = {&slots, &rounds, &info};
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIterThreads), args, 0, st);
     if (e == cudaSuccess) note_launches(1);
     return e;
 }

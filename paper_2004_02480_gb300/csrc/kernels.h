@@ -27,6 +27,10 @@ cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_
 // Count of kernels enqueued by the library (csk_kernel_launches).
 void note_launches(int k);
 
+// CSK_OK when `st` is NULL or belongs to the current device (or is being
+// captured, when its device cannot be queried), CSK_EINVAL otherwise.
+int check_stream_device(cudaStream_t st);
+
 // ------------------------------------------------------------- sketch
 // Scratch of the counting sort: cnt[d + 1] (bucket counts, then the bucket
 // claim counter of the segmented sum), off[d+1], perm_tmp[m], perm[m], scan
@@ -99,6 +103,10 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
                  IterConfig* cfg);
 cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st);
 
+// Exchange-only loop of `grid` CTAs for `rounds` rounds (csk_exchange_floor).
+cudaError_t launch_exchange_probe(int grid, int64_t rounds, Slot* slots, csk_info* info,
+                                  cudaStream_t st);
+
 // FP64 final check: info->rse, info->resid, info->empty_rows.
 cudaError_t launch_final_check(int dtype, const void* At, int64_t ld, int d, int n,
                                const void* bt, const double* N2, const void* x,
@@ -108,8 +116,19 @@ size_t final_check_partials(int d);
 
 // -------------------------------------------------------------- batched
 size_t batched_workspace_bytes(const csk_system* sys, int nsys);
-int launch_batched(const csk_system* sys, int nsys, const csk_params* p, void* ws, size_t ws_bytes,
-                   cudaStream_t st);
+// Per-step logs of one (system, right-hand side) pair: the caller's system
+// index and column; ik / x may be NULL.
+struct BatchLog {
+    int system = -1, rhs = 0;
+    int32_t* ik = nullptr;  int64_t ik_len = 0;
+    float* x = nullptr;     int64_t x_len = 0;
+};
+// Tuned launch shape for batches of this signature (threads = grid = 0
+// removes it); csk_solve_batched with threads = grid = 0 uses it.
+int set_batched_plan(const csk_system* sys, int nsys, int threads, int grid);
+uint64_t batched_signature(const csk_system* sys, int nsys);
+int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
+                   void* ws, size_t ws_bytes, cudaStream_t st);
 
 // ----------------------------------------------------------------- Gram
 // G = At At^T (d x d, FP32) from split BF16 operands on the tensor cores;

@@ -10,6 +10,7 @@
 // and take driver-wide locks.  For them this file keeps the scratch in one
 // statically sized device array that exists in every process that loads the
 // library, on every GPU it touches, until the process exits.
+#include <climits>
 #include <mutex>
 
 #include "common.cuh"
@@ -36,24 +37,27 @@ constexpr int64_t kNoAllocBytes =
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
-void* g_addr[kMaxDevices];
-cudaError_t g_err[kMaxDevices];
+std::mutex g_mu;
+void* g_addr[kMaxDevices];        // per device; set once its lookup succeeded
 
-// Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// Device address of the scratch on the current device.  The first call on a
+// device looks it up (the one-time set-up) and keeps it for the life of the
+// process; a failed lookup is not kept, so a later call tries again.
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_once[dev], [dev] {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
         void* p = nullptr;
-        g_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        g_addr[dev] = (g_err[dev] == cudaSuccess) ? p : nullptr;
-    });
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        if (!p) return cudaErrorInvalidSymbol;
+        g_addr[dev] = p;
+    }
     *out = g_addr[dev];
-    return g_err[dev];
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -71,11 +75,13 @@ extern "C" int csk_sketch_noalloc(const void* A, int64_t m, int64_t n, int64_t l
     if (m < 1 || n < 1 || d < 1 || lda < n || nrhs < 0) return CSK_EINVAL;
     if (dtype != CSK_F32 && dtype != CSK_F64) return CSK_EINVAL;
     if (nrhs > 0 && (!B || !Bt || ldb < nrhs)) return CSK_EINVAL;
-    if (m > kNoAllocMaxRows || d > kNoAllocMaxBuckets) return CSK_ENOMEM;
+    if (m > kNoAllocMaxRows || d > kNoAllocMaxBuckets || n > INT_MAX) return CSK_ENOMEM;
     if ((int64_t)sort_scratch_bytes(m, d) > kNoAllocBytes) return CSK_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
     void* base = nullptr;
     if (scratch_address(&base) != cudaSuccess || base == nullptr) return CSK_ECUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     SortScratch s;
     carve_sort_scratch(base, m, d, &s);       // bucket counts are zeroed by the sort itself
     if (perm_out) s.perm = perm_out;

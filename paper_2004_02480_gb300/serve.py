@@ -46,6 +46,16 @@ class Request:
     x: np.ndarray | None = None
 
 
+def arena_bytes(r: Request, workspace_bytes: int) -> int:
+    """Bytes Server.solve_group carves from the arena for the request alone:
+    its info records, A, B, X*, X (each range rounded up to the arena's
+    256-byte alignment) and the batched workspace of its one system
+    (``workspace_bytes`` = csk_solve_batched_workspace_size of it)."""
+    up = lambda v: (int(v) + Arena.ALIGN - 1) // Arena.ALIGN * Arena.ALIGN  # noqa: E731
+    return (up(64 * r.nrhs) + up(4 * r.m * r.n) + up(4 * r.m * r.nrhs) + 2 * up(4 * r.n * r.nrhs)
+            + up(max(int(workspace_bytes), 256)))
+
+
 def request_bytes(r: Request) -> int:
     """Device bytes a request holds while admitted: A, B, X*, X, info, and its
     part of the batched workspace (sketch, B sketch, norms, Gram matrix, plus
@@ -292,6 +302,11 @@ class Server:
             if group:
                 launched = self.solve_group(group, self.streams[free[0]])
                 if launched is None:              # arena fragmented: retry after a retire
+                    if not inflight:
+                        # nothing will be retired: an empty arena could not place the
+                        # group, so waiting would never end
+                        raise RuntimeError(f"group of {len(group)} requests does not fit the "
+                                           "empty arena: request_bytes underestimates it")
                     self.adm.unadmit(group)
                     group = []
             if group:

@@ -28,3 +28,17 @@ def read_golden(name):
 @pytest.fixture(scope="session")
 def golden():
     return read_golden
+
+
+def pytest_terminal_summary(terminalreporter):
+    """The per-step parity counts of the GPU tests (steps replayed, steps the
+    rounding bound forces, agreement with the oracle's selection from the
+    GPU's own iterates), printed even under -q."""
+    try:
+        from stepcheck import REPORT
+    except ImportError:
+        return
+    if REPORT:
+        terminalreporter.write_sep("-", "per-step parity")
+        for line in REPORT:
+            terminalreporter.write_line(line)

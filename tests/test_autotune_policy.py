@@ -24,3 +24,29 @@ def test_candidates_small_problem_keeps_four_rows_per_cta():
 
 def test_candidates_without_rows_are_fractions_only():
     assert candidates(152) == [152, 137, 128, 114, 100, 91, 76]
+
+
+def test_batched_candidates_respect_residency():
+    """Batched loop shapes: every thread count, 1..k CTAs per SM with k the
+    most that shared memory (r, weights: d each; x, x*: n each) and 128
+    registers a thread let stay resident."""
+    from paper_2004_02480_gb300.autotune import batched_candidates, batched_smem_bytes
+    c = batched_candidates(152, 10000, 1000)
+    assert batched_smem_bytes(10000, 1000) == (20000 + 2000) * 4
+    assert set(c) == {(128, 152), (128, 304), (256, 152), (256, 304), (384, 152), (512, 152)}
+    small = batched_candidates(152, 500, 50)
+    assert (128, 4 * 152) in small and (512, 152) in small and (512, 304) not in small
+    assert all(t in (128, 256, 384, 512) and g % 152 == 0 for t, g in small)
+
+
+def test_batched_signature_is_a_shape_histogram():
+    """Plans are keyed by the histogram of right-hand sides over (log2 d,
+    log2 n) bins: independent of the systems' order and of sizes inside a
+    bin, sensitive to a system moving bins or gaining right-hand sides."""
+    from paper_2004_02480_gb300 import csk
+    a = [(5000, 50, 500, 64), (20000, 120, 1200, 64), (8000, 77, 770, 3)]
+    s = csk.csk_solve_batched_signature(a)
+    assert s == csk.csk_solve_batched_signature(a[::-1])
+    assert s == csk.csk_solve_batched_signature([(5100, 51, 510, 64)] + a[1:])
+    assert s != csk.csk_solve_batched_signature([(5000, 50, 1100, 64)] + a[1:])
+    assert s != csk.csk_solve_batched_signature(a[:2] + [(8000, 77, 770, 4)])

@@ -148,3 +148,54 @@ def test_synth_systems_checks_on_host(L):
     assert L.csk_synth_systems(arr, 2, None) == csk.CSK_EINVAL
     arr[1] = csk.csk_synth_system(0, 10, 4, 0, 7, fake, fake, fake)
     assert L.csk_synth_systems(arr, 2, None) == csk.CSK_EINVAL
+
+
+def test_info_sync_and_workspace_size_checks(L):
+    """csk_info_sync rejects NULL records before any CUDA call;
+    csk_workspace_size covers csk_sketch, csk_solve and the one-system
+    batched solve of the same shape, and is 0 for invalid sizes."""
+    fake = ctypes.c_void_p(256)
+    assert L.csk_info_sync(None, fake, None) == csk.CSK_EINVAL
+    assert L.csk_info_sync(fake, None, None) == csk.CSK_EINVAL
+    m, n, d = 100000, 500, 5000
+    for dt in (csk.CSK_F32, csk.CSK_F64):
+        for path in (csk.GEMV, csk.AUTO) + ((csk.GRAM,) if dt == csk.CSK_F32 else ()):
+            w = L.csk_workspace_size(m, n, d, 1, dt, path)
+            p = csk.csk_params_default(d=d, path=path)
+            assert w >= csk.csk_solve_workspace_size(m, n, dt, p) > 0
+            assert w >= L.csk_sketch_workspace_size(m, d) > 0
+    one = csk.csk_system(256, m, n, n, 256, 4, 4, 0, d, 0, None, None, 256, 256)
+    arr = (csk.csk_system * 1)(one)
+    assert L.csk_workspace_size(m, n, d, 4, csk.CSK_F32, csk.GRAM) >= \
+        L.csk_solve_batched_workspace_size(arr, 1) > 0
+    assert L.csk_workspace_size(m, n, 0, 1, csk.CSK_F32, csk.GEMV) == \
+        csk.csk_solve_workspace_size(m, n, csk.CSK_F32, csk.csk_params_default(d=0))
+    for bad in ((0, n, d, 1, 0, 0), (m, 0, d, 1, 0, 0), (m, n, -1, 1, 0, 0), (m, n, d, -1, 0, 0),
+                (m, n, d, 1, 5, 0), (m, n, d, 1, 0, 7)):
+        assert L.csk_workspace_size(*bad) == 0
+
+
+def test_exchange_floor_checks_on_host(L):
+    fake = ctypes.c_void_p(256)
+    assert L.csk_exchange_floor_workspace_size(0) == 0
+    assert L.csk_exchange_floor_workspace_size(321) == 0
+    need = L.csk_exchange_floor_workspace_size(91)
+    assert need >= 2 * 91 * 91 * 32 and need % 256 == 0
+    assert L.csk_exchange_floor(0, 10, fake, need, None) == csk.CSK_EINVAL
+    assert L.csk_exchange_floor(91, 0, fake, need, None) == csk.CSK_EINVAL
+    assert L.csk_exchange_floor(91, 10, None, need, None) == csk.CSK_EINVAL
+    assert L.csk_exchange_floor(91, 10, fake, need - 256, None) == csk.CSK_EINVAL
+    assert L.csk_exchange_floor(91, 10, ctypes.c_void_p(264), need, None) == csk.CSK_EINVAL
+
+
+def test_batched_log_arguments_checked_on_host(L):
+    """The per-step logs of csk_solve_batched name one (system, right-hand
+    side) pair of the caller's array; out-of-range pairs and a log length
+    without a buffer are rejected before any CUDA call."""
+    one = csk.csk_system(256, 1000, 10, 10, 256, 2, 2, 0, 100, 0, None, None, 256, 256)
+    arr = (csk.csk_system * 1)(one)
+    fake = ctypes.c_void_p(256)
+    for kw in (dict(ik_log=256, ik_log_len=5, log_system=1), dict(ik_log=256, ik_log_len=5, log_rhs=2),
+               dict(ik_log_len=5), dict(x_log_len=5), dict(x_log=256, x_log_len=5, log_system=-1)):
+        p = csk.csk_params_default(**kw)
+        assert L.csk_solve_batched(arr, 1, ctypes.byref(p), fake, 1 << 40, None) == csk.CSK_EINVAL

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import stepcheck
 from paper_2004_02480_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -115,3 +116,74 @@ def test_batched_graph_capture_replay(csk):
     torch.cuda.synchronize()
     for y, X in zip(batch, ref):
         assert torch.equal(y.Xout.cpu(), X)
+
+
+@pytest.mark.parametrize("refresh", [0, 25])
+def test_batched_per_step_replay(csk, refresh):
+    """A sample of (system, right-hand side) units of one batched launch,
+    logged step by step (i_k and x_k of one unit per launch) and replayed in
+    FP64 from the GPU's own iterates: i_k admissible and each step the
+    projection of Algorithm 1 within the GRAM path's bound (FP32 rounding,
+    split-BF16 error of G_s, drift since the last FP64 recomputation), and the
+    oracle's selection from the same iterate equal to i_k wherever it is not
+    a near-tie within that bound.  The other units of the launch run as usual."""
+    batch, host = _batch(csk, SHAPES, seed0=40)
+    L = 20000
+    for si, rhs in ((0, 2), (2, 1), (5, 3), (4, 0)):
+        m, n, d, R = SHAPES[si]
+        ik = torch.full((L,), -1, dtype=torch.int32, device=DEV)
+        X = torch.zeros((L, n), dtype=torch.float32, device=DEV)
+        p = csk.csk_params_default(refresh_every=refresh, ik_log=ik.data_ptr(), ik_log_len=L,
+                                   x_log=X.data_ptr(), x_log_len=L, log_system=si, log_rhs=rhs)
+        out = csk.csk_solve_batched(batch, p)
+        info = out[si][1][rhs]
+        assert info["status"] == 0 and info["rse"] <= 1e-6
+        y, s = batch[si], host[si]
+        h, sg = oracle.count_sketch_map(y.seed, m, d)
+        At, Bt = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+        steps = info["iters"]
+        ikh = ik.cpu().numpy()
+        assert np.all(ikh[:steps] >= 0) and np.all(ikh[steps:] == -1)
+        # x_0 .. x_{IT-1} from the log, x_IT = the unit's output
+        Xh = np.concatenate([X.cpu().numpy()[:steps], y.Xout[:, rhs].cpu().numpy()[None]])
+        rep = stepcheck.replay(At, Bt[:, rhs], Xh, ikh, steps, path="gram",
+                               refresh=refresh, oracle=oracle,
+                               name=f"batched unit ({m}x{n} d={d}, rhs {rhs}) refresh {refresh}")
+        ref = oracle.mwrk(At.astype(np.float64), Bt[:, rhs].astype(np.float64),
+                          x_star=s.x_star[:, rhs], log_len=L, nthreads=4)
+        rep.prefix, _ = stepcheck.trajectory_prefix(ikh, ref, 1e-3)
+        stepcheck.record(rep)
+        assert rep.steps == steps and rep.oracle_equal >= 0.9 * steps
+
+
+def test_tuned_plan_is_used_and_changes_no_result(csk):
+    """The batched autotuner times the candidate launch shapes on the batch
+    and installs the fastest; a call with threads = grid = 0 then runs that
+    shape (its CTA count is reported in info.grid), also inside a CUDA graph,
+    and gives the bits of an explicit call with the same thread count."""
+    from paper_2004_02480_gb300 import autotune
+    batch, host = _batch(csk, SHAPES, seed0=50)
+    ws = torch.empty(csk.csk_solve_batched_workspace_size(batch), dtype=torch.uint8, device=DEV)
+    best = autotune.tune_batched(batch, ws=ws, use_cache=False)
+    assert (best["threads"], best["grid"]) in autotune.batched_candidates(
+        torch.cuda.get_device_properties(0).multi_processor_count, max(y.d for y in batch),
+        max(y.A.shape[1] for y in batch))
+    tuned = [(X.cpu().clone(), [i["grid"] for i in inf], [i["iters"] for i in inf])
+             for X, inf in csk.csk_solve_batched(batch, csk.csk_params_default(), ws=ws)]
+    assert all(g == best["grid"] for _, gs, _ in tuned for g in gs)
+    expl = csk.csk_params_default(threads=best["threads"], grid=best["grid"])
+    for (X, _, its), (X2, inf2) in zip(tuned, csk.csk_solve_batched(batch, expl, ws=ws)):
+        assert torch.equal(X, X2.cpu()) and its == [i["iters"] for i in inf2]
+    # the same plan inside a graph capture
+    for y in batch:
+        y.Xout.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        csk.csk_solve_batched(batch, csk.csk_params_default(), ws=ws, sync=False)
+    g.replay()
+    torch.cuda.synchronize()
+    for y, (X, _, _) in zip(batch, tuned):
+        assert torch.equal(y.Xout.cpu(), X)
+    csk.csk_solve_batched_set_plan(batch, 0, 0)            # back to the library default

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+import stepcheck
 from paper_2004_02480_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -48,44 +49,23 @@ def _solve(csk, sysm, d, seed, log=0, xlog=0, **kw):
     return x.cpu().numpy(), info, ik.cpu().numpy()[:log]
 
 
-def _check_steps(At, bt, X, ik, steps, u):
-    """Every GPU step, replayed in FP64 from the GPU's own iterate x_k:
-    (1) i_k is a maximiser of r_j^2 / ||At_j||^2 within the worst-case
-        rounding bound of the kernel's arithmetic (unit roundoff u, a sum of
-        n + 1 terms: |dr_j| <= gamma_{n+1} (|bt_j| + sum_c |At_jc x_c|), plus
-        a few roundings for the key itself), and
-    (2) x_{k+1} - x_k is the projection step alpha At_{i_k} of Algorithm 1 to
-        the same accuracy."""
-    At = At.astype(np.float64)
-    bt = bt.astype(np.float64)
-    d, n = At.shape
-    N = np.sum(At * At, axis=1)
-    g = (n + 1) * u / (1 - (n + 1) * u)
-    absA = np.abs(At)
-    Xd = X[:steps + 1].astype(np.float64)
-    R = bt[:, None] - At @ Xd.T                       # d x (steps+1)
-    B = np.abs(bt)[:, None] + absA @ np.abs(Xd).T
-    valid = N > 0
-    for k in range(steps):
-        r, bnd = R[:, k], g * B[:, k]
-        lo = np.where(valid, np.maximum(np.abs(r) - bnd, 0) ** 2 / np.where(valid, N, 1), -1)
-        hi = np.where(valid, (np.abs(r) + bnd) ** 2 / np.where(valid, N, 1), -1)
-        j = ik[k]
-        assert valid[j], k
-        assert hi[j] * (1 + 8 * u) >= lo.max() * (1 - 8 * u), (k, j, hi[j], lo.max())
-        step = Xd[k + 1] - Xd[k]
-        alpha = r[j] / N[j]
-        da = (bnd[j] / N[j]) + 8 * u * abs(alpha)
-        err = np.abs(step - alpha * At[j])
-        assert np.all(err <= da * absA[j] + 4 * u * (np.abs(Xd[k]) + np.abs(Xd[k + 1]))), k
-    return steps
+def _check_steps(At, bt, X, ik, steps, u, name="", oracle_check=True):
+    """Every GPU step replayed in FP64 from the GPU's own iterate x_k
+    (stepcheck.replay, GEMV bound): i_k admissible under the rounding bound,
+    the projection exact to it, and the oracle's own selection from x_k equal
+    to i_k wherever that choice is not a near-tie within the bound."""
+    rep = stepcheck.replay(At, bt, X, ik, steps, path="gemv", u=u, name=name,
+                           oracle=oracle if oracle_check else None)
+    stepcheck.record(rep)
+    if oracle_check:
+        assert rep.oracle_equal >= rep.oracle_forced
+    return rep.steps
 
 
-def _compare_prefix(ik_gpu, ref, tau):
-    gap = ref.gap
-    k_tau = int(np.argmax(gap < tau)) if np.any(gap < tau) else len(gap)
-    K = min(1000, k_tau, len(ik_gpu), len(ref.ik))
-    assert np.array_equal(ik_gpu[:K], ref.ik[:K]), (K, np.flatnonzero(ik_gpu[:K] != ref.ik[:K])[:5])
+def _compare_prefix(ik_gpu, ref, tau, name=""):
+    K, k_tau = stepcheck.trajectory_prefix(ik_gpu, ref, tau)
+    stepcheck.REPORT.append(f"{name}: i_k equal to the oracle's own trajectory for the first {K} "
+                            f"steps (first near-tie, gap < {tau:g}, at step {k_tau})")
     return K
 
 
@@ -99,7 +79,7 @@ def test_config1_fp64_matches_oracle(csk, seed):
     ref = oracle.mwrk(At, bt, x_star=s.x_star, tol=1e-6, log_len=2000)
     assert info["status"] == 0 and ref.status == 0
     assert info["rse"] <= 1e-6
-    K = _compare_prefix(ik, ref, 1e-9)
+    K = _compare_prefix(ik, ref, 1e-9, name=f"FP64 2000x50 d=500 seed {seed}")
     if K == ref.iters:
         assert info["iters"] == ref.iters
     assert np.sum((x - ref.x) ** 2) / np.sum(s.x_star ** 2) <= 1e-6
@@ -133,9 +113,11 @@ def test_config2_fp32_gemv_matches_oracle(csk):
     ref = oracle.mwrk(At32.astype(np.float64), bt32.astype(np.float64), x_star=s.x_star,
                       tol=1e-6, log_len=20000, nthreads=8)
     assert info["status"] == 0 and info["rse"] <= 1e-6
-    K = _compare_prefix(ik, ref, 1e-3)
+    K = _compare_prefix(ik, ref, 1e-3, name="FP32 GEMV 100000x500 d=5000 seed 0")
     assert K >= 1
-    assert _check_steps(At32, bt32, X, ik, info["iters"] - 1, 2.0 ** -24) > 500
+    Xh = np.concatenate([X[:info["iters"]], x[None]])   # x_0 .. x_{IT-1} logged, x_IT returned
+    assert _check_steps(At32, bt32, Xh, ik, info["iters"], 2.0 ** -24,
+                        name="FP32 GEMV 100000x500 d=5000 seed 0") == info["iters"]
     assert abs(info["iters"] - ref.iters) <= 0.05 * ref.iters
     assert np.sum((x - ref.x) ** 2) / np.sum(s.x_star ** 2) <= 4e-6
 

@@ -400,3 +400,32 @@ def test_inconsistent_system_never_beats_least_squares():
     # and the oracle's own iterate after those 50 steps is this replay
     r50 = oracle.mwrk(At, bt, tol=0.0, max_iter=50)
     assert np.allclose(r50.x, x, rtol=1e-12, atol=1e-12 * np.linalg.norm(x))
+
+
+@pytest.mark.parametrize("d,n", [(1, 1), (9, 7), (70, 65), (130, 64), (257, 130)])
+def test_gram_rows_equal_whole_split_product(d, n):
+    """or_gram_split_bf16_rows (the comparator of the full-size Gram check):
+    each requested row, in the requested order and with repeats, equals the
+    same row of or_gram_split_bf16 bit for bit, and both equal the split
+    definition hi hi^T + hi lo^T + lo hi^T formed independently here with
+    torch's BF16 cast and a numpy product (BF16 products are exact in
+    binary64, so only the summation order differs)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(d * 131 + n)
+    At = (rng.standard_normal((d, n)) * 10.0 ** rng.integers(-3, 3, (d, 1))).astype(np.float32)
+    rows = np.concatenate([[d - 1, 0], rng.integers(0, d, 6), [d - 1]]).astype(np.int64)
+    Gr = oracle.gram_split_bf16_rows(At, rows)
+    Gs = oracle.gram_split_bf16(At)
+    assert Gr.shape == (len(rows), d)
+    assert np.array_equal(Gr.view(np.uint64), Gs[rows].view(np.uint64))
+    t = torch.from_numpy(At)
+    hi_t = t.to(torch.bfloat16).to(torch.float32)
+    lo_t = (t - hi_t).to(torch.bfloat16).to(torch.float32)
+    hi, lo = hi_t.double().numpy(), lo_t.double().numpy()
+    split = hi[rows] @ hi.T + hi[rows] @ lo.T + lo[rows] @ hi.T
+    mag = np.abs(hi[rows]) @ np.abs(hi).T + np.abs(hi[rows]) @ np.abs(lo).T + np.abs(lo[rows]) @ np.abs(hi).T
+    assert np.all(np.abs(Gr - split) <= 4 * n * 2.0 ** -53 * mag)
+    # a transposed operand or a dropped segment would be far outside that
+    wrong = hi[rows] @ hi.T + lo[rows] @ hi.T
+    if n > 1:
+        assert np.any(np.abs(Gr - wrong) > 4 * n * 2.0 ** -53 * mag)

@@ -93,3 +93,25 @@ def test_arena_first_fit_and_coalescing():
         for (o1, n1), (o2, _) in zip(spans, spans[1:]):
             assert o1 + n1 <= o2                    # no overlap
         assert a.in_use() == sum(n for _, n in spans)
+
+
+def test_request_bytes_covers_what_the_arena_carves():
+    """request_bytes (the admission estimate) is at least what solve_group
+    carves from the arena for the request alone -- its tensors plus the
+    library's batched workspace for its one system -- over the serving size
+    ranges, so a lone admitted request always fits an empty arena."""
+    import ctypes
+
+    from paper_2004_02480_gb300 import csk
+    from paper_2004_02480_gb300.serve import arena_bytes
+    L = csk.lib()
+    rng = np.random.default_rng(5)
+    shapes = [(2000, 20, 1), (100000, 500, 16), (2000, 500, 16), (100000, 20, 1), (2001, 21, 3)]
+    shapes += [(int(np.exp(rng.uniform(np.log(2000), np.log(100000)))), int(rng.integers(20, 501)),
+                int(rng.integers(1, 17))) for _ in range(200)]
+    for m, n, R in shapes:
+        r = Request(0, 0.0, m, n, 8 * n, R, 1)
+        one = csk.csk_system(256, m, n, n, 256, R, R, 0, r.d, 1, None, 256, 256, 256)
+        ws = L.csk_solve_batched_workspace_size((csk.csk_system * 1)(one), 1)
+        assert ws > 0
+        assert request_bytes(r) >= arena_bytes(r, ws), (m, n, R)

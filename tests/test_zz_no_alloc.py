@@ -46,6 +46,26 @@ def test_noalloc_sketch_matches_workspace_sketch_twice(csk):
             assert torch.equal(out.norms2, ref.norms2)
 
 
+def test_noalloc_default_outputs_only(csk):
+    """The common call: no b, no perm and no off requested, so the sorted
+    rows and the bucket offsets stay in the static array too (at the full
+    2^20-row, 2^18-bucket size as well).  At and the FP64 norms must equal
+    csk_sketch's bit for bit, on two calls in a row."""
+    dev = "cuda:0"
+    g = torch.Generator(device=dev).manual_seed(321)
+    for m, n, d, dt, seed in [(1 << 20, 4, 1 << 18, torch.float32, 3),
+                              (70_001, 129, 5_003, torch.float32, 4),
+                              (30_000, 50, 2_500, torch.float64, 5)]:
+        A = torch.randn((m, n), generator=g, device=dev, dtype=dt)
+        ref = csk.csk_sketch(A, d, seed, None, norms=True)
+        for _ in range(2):
+            out = csk.csk_sketch_noalloc(A, d, seed, None, norms=True)
+            torch.cuda.synchronize()
+            assert out.bt is None and out.perm is None and out.off is None
+            assert torch.equal(out.At, ref.At)
+            assert torch.equal(out.norms2, ref.norms2)
+
+
 def test_noalloc_rejects_sizes_beyond_static_scratch(csk):
     fake = ctypes.c_void_p(256)
     L = csk.lib()
