@@ -154,9 +154,8 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     if (d > 0) {
         SortScratch s;
         carve_sort_scratch(w + L.sort, m, d, &s);
-        if (launch_bucket_group(m, d, params->seed, s, st) != cudaSuccess) return CSK_ECUDA;
-        if (launch_segsum(dtype, A, lda, m, (int)n, b, 1, 1, s, (int)d, params->seed,
-                          w + L.At, w + L.bt, N2, st) != cudaSuccess)
+        if (launch_sketch(dtype, A, lda, m, (int)n, b, 1, 1, s, (int)d, params->seed, w + L.At,
+                          w + L.bt, N2, st) != cudaSuccess)
             return CSK_ECUDA;
         At = w + L.At;
         bt = w + L.bt;
@@ -377,9 +376,8 @@ int csk_sketch(const void* A, int64_t m, int64_t n, int64_t lda, const void* B, 
     carve_sort_scratch(ws, m, d, &s);
     if (perm_out) s.perm = perm_out;
     if (off_out) s.off = off_out;
-    if (launch_bucket_group(m, d, seed, s, st) != cudaSuccess) return CSK_ECUDA;
-    if (launch_segsum(dtype, A, lda, m, (int)n, nrhs > 0 ? B : nullptr, ldb, nrhs, s, (int)d,
-                      seed, At, Bt, norms2_out, st) != cudaSuccess)
+    if (launch_sketch(dtype, A, lda, m, (int)n, nrhs > 0 ? B : nullptr, ldb, nrhs, s, (int)d, seed,
+                      At, Bt, norms2_out, st) != cudaSuccess)
         return CSK_ECUDA;
     return CSK_OK;
 }

@@ -481,8 +481,7 @@ int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const B
         float* Bt = reinterpret_cast<float*>(w + L.Bt[i]);
         double* N2 = reinterpret_cast<double*>(w + L.N2[i]);
         float* G = reinterpret_cast<float*>(w + L.G[i]);
-        if (launch_bucket_group(y.m, y.d, y.seed, s, st) != cudaSuccess) return CSK_ECUDA;
-        if (launch_segsum(CSK_F32, y.A, y.lda, y.m, (int)y.n, y.B, y.ldb, y.nrhs, s, (int)y.d,
+        if (launch_sketch(CSK_F32, y.A, y.lda, y.m, (int)y.n, y.B, y.ldb, y.nrhs, s, (int)y.d,
                           y.seed, At, Bt, N2, st) != cudaSuccess)
             return CSK_ECUDA;
         if (launch_gram_split_bf16(At, (int)y.d, (int)y.n, N2, G, gram_ld((int)y.d), w + L.gscr,

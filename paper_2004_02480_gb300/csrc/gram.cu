@@ -52,12 +52,21 @@ inline int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return csk::mbar_wait(bar, parity, kWaitLimit);
 }
+// L2 policy for the BF16 operands: keep them resident (evict last).  The
+// operands (d_pad x k_pad x 2 x 2 bytes, 82 MB at d = 20000, n = 1000) fit in
+// the 129 MB L2, but the 1.6 GB of G written meanwhile would otherwise push
+// them out, and a stage that misses L2 stalls the tensor pipe.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int c0, int c1) {
+                                            int c0, int c1, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "l"(policy)
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -192,6 +201,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer
+            const uint64_t pol = l2_evict_last_policy();
             int64_t g = 0;                 // chunk counter over all tiles of this CTA
             int64_t issued = 0;
             bool ok = true;
@@ -211,8 +221,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                     const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     mbar_expect_tx(fb, STAGE_BYTES);
-                    tma_load_2d(sa, ma, fb, kc * BK, bi * BM);
-                    tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN);
+                    tma_load_2d(sa, ma, fb, kc * BK, bi * BM, pol);
+                    tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN, pol);
                     issued = g + 1;
                 }
             }

@@ -56,6 +56,13 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
                           int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
                           void* At, void* Bt, double* N2, cudaStream_t st);
 
+// The whole sketch: the counting-sort path (launch_bucket_group, then
+// launch_segsum), or for FP32 sketches with small buckets the bucket-owner
+// path (a hash pass and one kernel, no global sort).  Same outputs, same bits.
+cudaError_t launch_sketch(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
+                          int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
+                          void* At, void* Bt, double* N2, cudaStream_t st);
+
 // FP64 squared row norms of a (rows x n, ld) matrix (unsketched path).
 cudaError_t launch_row_norms(int dtype, const void* A, int64_t ld, int rows, int n,
                              double* N2, cudaStream_t st);

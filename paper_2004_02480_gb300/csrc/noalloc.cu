@@ -86,9 +86,8 @@ extern "C" int csk_sketch_noalloc(const void* A, int64_t m, int64_t n, int64_t l
     carve_sort_scratch(base, m, d, &s);       // bucket counts are zeroed by the sort itself
     if (perm_out) s.perm = perm_out;
     if (off_out) s.off = off_out;
-    if (launch_bucket_group(m, d, seed, s, st) != cudaSuccess) return CSK_ECUDA;
-    if (launch_segsum(dtype, A, lda, m, (int)n, nrhs > 0 ? B : nullptr, ldb, nrhs, s, (int)d,
-                      seed, At, Bt, norms2_out, st) != cudaSuccess)
+    if (launch_sketch(dtype, A, lda, m, (int)n, nrhs > 0 ? B : nullptr, ldb, nrhs, s, (int)d, seed,
+                      At, Bt, norms2_out, st) != cudaSuccess)
         return CSK_ECUDA;
     return CSK_OK;
 }

@@ -153,3 +153,22 @@ def test_sketch_full_size_precision_form_sampled(csk):
         Atj, _ = oracle.sketch_f32_same_order(Aj, None, np.zeros(len(members), np.int32),
                                               sg[members], 1)
         assert np.array_equal(Atg[j], Atj[0])
+
+
+@pytest.mark.parametrize("env", [{"CSK_SKETCH_PATH": "sort"}, {"CSK_SKETCH_PATH": "own"},
+                                 {"CSK_SKETCH_PATH": "own", "CSK_SKETCH_OWN_CAP": "256"},
+                                 {"CSK_SKETCH_PATH": "own", "CSK_SKETCH_OWN_CAP": "16"}])
+def test_sketch_paths_bit_exact(csk, env):
+    """The counting-sort path and the bucket-owner FP32 path (forced for
+    every shape, including buckets of ~150 rows), the latter also with a
+    per-CTA row list of 256 and of 16 rows -- so its sub-range rescans and
+    its large-bucket ordering by ballot compaction run -- give the oracle's
+    offsets, permutation, At and Bt bit for bit (child process: the path is
+    read from the environment once)."""
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.join(here, "sketch_paths_check.py")],
+                       env={**os.environ, **env}, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
