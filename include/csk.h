@@ -63,15 +63,27 @@ typedef enum { CSK_F32 = 0, CSK_F64 = 1 } csk_dtype;
  *        the tensor cores in split BF16 (hi*hi + hi*lo + lo*hi, FP32
  *        accumulation), r_{i_k} set to 0 exactly, and an FP64 recomputation
  *        of r every refresh_every steps.  Equal to GEMV in exact arithmetic.
- *  AUTO: the library picks (GEMV when the sketch fits on chip). */
-typedef enum { CSK_RESID_GEMV = 0, CSK_RESID_GRAM = 1, CSK_RESID_AUTO = 2 } csk_resid;
+ *  AUTO: the library picks (GEMV when the sketch fits on chip).
+ *  UPDATE: the residual-update form of Remark 1: the loop keeps r and sets
+ *        r_{k+1} = r_k - alpha_k At At_{i_k}^T (a GEMV of At against the
+ *        chosen row, same bytes per step as GEMV), r_{i_k} = 0 exactly, with
+ *        r recomputed as bt - At x at the first step and every refresh_every
+ *        steps.  Runs the streamed loop (n a multiple of 16 bytes, n <= 1024
+ *        FP32 / 512 FP64); equal to GEMV in exact arithmetic. */
+typedef enum {
+    CSK_RESID_GEMV = 0,
+    CSK_RESID_GRAM = 1,
+    CSK_RESID_AUTO = 2,
+    CSK_RESID_UPDATE = 3
+} csk_resid;
 
 typedef struct {
     int64_t d;              /* sketch rows; 0 = no sketch (MWRK on A, Remark 1) */
     uint64_t seed;          /* sketch seed (Definition 1)                       */
     double tol;             /* RES tolerance, default 1e-6 (Section 3)           */
     int64_t max_iter;       /* step cap, default 20000 (Section 3)               */
-    int32_t refresh_every;  /* GRAM path: FP64 residual refresh period, 0 = off  */
+    int32_t refresh_every;  /* GRAM: FP64 residual refresh period; UPDATE: period
+                               of the recomputation bt - At x; 0 = off          */
     int32_t path;           /* csk_resid                                         */
     int64_t spin_limit;     /* polls per inter-CTA wait before CSK_ETIMEOUT,
                                0 = default (about a second)                      */

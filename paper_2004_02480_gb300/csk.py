@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "csk.h")
 CSK_OK, CSK_MAXITER = 0, 1
 CSK_EINVAL, CSK_ENOMEM, CSK_ETIMEOUT, CSK_ENUMERIC, CSK_ECUDA, CSK_EUNSUPPORTED = -1, -2, -3, -4, -5, -6
 CSK_F32, CSK_F64 = 0, 1
-GEMV, GRAM, AUTO = 0, 1, 2
+GEMV, GRAM, AUTO, UPDATE = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None

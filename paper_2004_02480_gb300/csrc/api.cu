@@ -79,7 +79,7 @@ int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk
     if (d < 0 || !(params->tol >= 0.0) || params->max_iter < 0) return CSK_EINVAL;
     if (params->ik_log_len < 0 || (params->ik_log_len > 0 && !params->ik_log)) return CSK_EINVAL;
     if (params->x_log_len < 0 || (params->x_log_len > 0 && !params->x_log)) return CSK_EINVAL;
-    if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_AUTO) return CSK_EINVAL;
+    if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_UPDATE) return CSK_EINVAL;
     if (params->grid < 0 || params->refresh_every < 0) return CSK_EINVAL;
     if (params->gemv_variant < 0 || params->gemv_variant > 3) return CSK_EINVAL;
     if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
@@ -462,7 +462,7 @@ size_t csk_workspace_size(int64_t m, int64_t n, int64_t d, int32_t nrhs, int32_t
                           int32_t resid) {
     if (m < 1 || n < 1 || d < 0 || nrhs < 0) return 0;
     if (dtype != CSK_F32 && dtype != CSK_F64) return 0;
-    if (resid < CSK_RESID_GEMV || resid > CSK_RESID_AUTO) return 0;
+    if (resid < CSK_RESID_GEMV || resid > CSK_RESID_UPDATE) return 0;
     csk_params p;
     csk_params_default(&p);
     p.d = d;

@@ -58,8 +58,7 @@ __device__ __forceinline__ void st_relaxed_v2(uint64_t* p, uint64_t a, uint64_t 
 __device__ __forceinline__ void ld_relaxed_v2(const uint64_t* p, uint64_t& a, uint64_t& b) {
     asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
-__device__ __forceinline__ Slot* mailbox(Slot* slots, uint32_t round, int dest, int src) {
-    const int G = gridDim.x;
+__device__ __forceinline__ Slot* mailbox(Slot* slots, uint32_t round, int dest, int src, int G) {
     return slots + ((size_t)(round & 1u) * G + dest) * G + src;
 }
 
@@ -85,15 +84,18 @@ __device__ __forceinline__ void prefetch_row(const RowPrefetch& pf, int32_t idx)
 // FP32: four stamped words per slot.
 // With `acquire`, every polling thread fences after seeing the new round, so
 // plain data the other CTAs stored before publishing is visible afterwards.
+// Among G participants, this CTA being participant b (by default the whole
+// grid, CTA b = blockIdx.x).
 __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>& c,
                                          int64_t spin_limit, int fault_inject, csk_info* info,
                                          RedShared<float>& sh, int& par, bool acquire = false,
-                                         const RowPrefetch& pf = RowPrefetch()) {
-    const int G = gridDim.x, b = blockIdx.x;
+                                         const RowPrefetch& pf = RowPrefetch(), int G = 0,
+                                         int b = -1) {
+    if (G == 0) { G = gridDim.x; b = blockIdx.x; }
     const uint64_t stamp = (uint64_t)(round + 1u) << 32;
     if (!(fault_inject && b == 0))
         for (int t = threadIdx.x; t < G; t += blockDim.x) {
-            uint64_t* w = reinterpret_cast<uint64_t*>(mailbox(slots, round, t, b));
+            uint64_t* w = reinterpret_cast<uint64_t*>(mailbox(slots, round, t, b, G));
             st_relaxed_v2(w, stamp | __float_as_uint(c.key), stamp | __float_as_uint(c.alpha));
             st_relaxed_v2(w + 2, stamp | __float_as_uint(c.stat), stamp | (uint32_t)c.idx);
         }
@@ -101,7 +103,7 @@ __device__ __forceinline__ bool exchange(Slot* slots, uint32_t round, Red<float>
     g.key = -1.0f; g.alpha = 0.0f; g.stat = 0.0f; g.idx = INT_MAX;
     int timed_out = 0;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
-        const uint64_t* w = reinterpret_cast<const uint64_t*>(mailbox(slots, round, b, t));
+        const uint64_t* w = reinterpret_cast<const uint64_t*>(mailbox(slots, round, b, t, G));
         uint64_t v0, v1, v2, v3;
         int64_t spins = 0;
         for (;;) {
@@ -639,11 +641,20 @@ struct StreamShape {
     static constexpr int ROWS = kWarps * RPB;
 };
 
-size_t stream_smem_bytes(int R, int n, int esize, int rows_per_blk, int stages) {
-    return (size_t)stages * rows_per_blk * n * esize + (size_t)2 * ((R + 3) & ~3) * esize;
+// Shared memory: the ring, then bt and the row weights of the CTA's rows, and
+// with UPD the stored residuals of those rows.
+size_t stream_smem_bytes(int R, int n, int esize, int rows_per_blk, int stages, bool upd) {
+    return (size_t)stages * rows_per_blk * n * esize + (size_t)(upd ? 3 : 2) * ((R + 3) & ~3) * esize;
 }
 
-template <typename T, int CPL>
+// UPD: the residual-update form of Remark 1.  The CTA keeps r for its rows;
+// a step takes the dot products of its rows with the previous step's chosen
+// row At_{i} (kept in registers like x) instead of with x, and sets
+// r_j = r_j - alpha * (At_j . At_i), r_i = 0 (exact arithmetic gives 0).  The
+// first step, and every refresh_every-th, recomputes r = bt - At x.  Same
+// bytes streamed per step as the GEMV form; only the dot products' second
+// operand differs.
+template <typename T, int CPL, bool UPD>
 __global__ void __launch_bounds__(kIterThreads, 1)
 k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     constexpr int RPB = StreamShape<T, CPL>::RPB, SR = StreamShape<T, CPL>::ROWS;
@@ -664,6 +675,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     T* ring = reinterpret_cast<T*>(dsm);
     T* bts = ring + nst * blk_elems;
     T* w2s = bts + ((R + 3) & ~3);
+    T* rst = w2s + ((R + 3) & ~3);            // UPD: the rows' residuals
     const T* At = static_cast<const T*>(p.At);
     const T* bt = static_cast<const T*>(p.bt);
     const T* x0 = static_cast<const T*>(p.x0);
@@ -714,12 +726,14 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     int stalled = 0;
     if (tid == 0 && nblk > 0 && !refill(nst)) stalled = 1;
 
-    T xr[CPL][V], xsr[CPL][V];
+    T xr[CPL][V], xsr[CPL][V], ar[CPL][V];   // ar (UPD): the previous step's chosen row
+    T aprev = T(0);                           // UPD: its step length
+    int32_t iprev = -1;                       //      and its row
 #pragma unroll
     for (int i = 0; i < CPL; ++i) {
         const int c = lane + 32 * i;
 #pragma unroll
-        for (int e = 0; e < V; ++e) { xr[i][e] = T(0); xsr[i][e] = T(0); }
+        for (int e = 0; e < V; ++e) { xr[i][e] = T(0); xsr[i][e] = T(0); ar[i][e] = T(0); }
         if (x0 && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(x0)[c], xr[i]);
         if (xstar && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(xstar)[c], xsr[i]);
     }
@@ -733,6 +747,9 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     for (;;) {
         Red<T> c;
         c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
+        // dot products against x (GEMV form, and the UPD form's recomputation
+        // steps) or against the previous chosen row (UPD update steps)
+        const bool use_x = !UPD || k == 0 || (p.refresh_every > 0 && k % p.refresh_every == 0);
         for (int blk = 0; blk < nblk && !stalled; ++blk, ++g) {
             const int s = cs;
             const uint32_t lap = clap;
@@ -756,7 +773,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                         T a[V];
                         Chunk<T>::get(row[cc], a);
 #pragma unroll
-                        for (int e = 0; e < V; ++e) acc = fma(a[e], xr[i][e], acc);
+                        for (int e = 0; e < V; ++e) acc = fma(a[e], use_x ? xr[i][e] : ar[i][e], acc);
                     }
                 }
                 dot[u] = acc;
@@ -770,7 +787,10 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 const int u = transpose_row<RPB>(lane);
                 const int q = q0 + warp + kWarps * u;
                 if (transpose_rep<RPB>(lane) && q < nr) {
-                    const T r = bts[q] - sum;
+                    T r;
+                    if (!UPD || use_x) r = bts[q] - sum;
+                    else r = (r0 + q == iprev) ? T(0) : fma(-aprev, sum, rst[q]);
+                    if (UPD) rst[q] = r;
                     const T w = w2s[q];
                     if (!below_zero(w)) {
                         const T key = r * r * w;
@@ -823,9 +843,13 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
                 T v[V];
                 Chunk<T>::get(__ldg(arow + cc), v);
 #pragma unroll
-                for (int e = 0; e < V; ++e) xr[i][e] = fma(c.alpha, v[e], xr[i][e]);
+                for (int e = 0; e < V; ++e) {
+                    xr[i][e] = fma(c.alpha, v[e], xr[i][e]);
+                    if (UPD) ar[i][e] = v[e];
+                }
             }
         }
+        if (UPD) { aprev = c.alpha; iprev = c.idx; }
         ++k;
     }
     // no bulk copy may still be writing shared memory when the CTA exits
@@ -858,15 +882,20 @@ const void* gemv_kernel(int dtype, int rows_per_cta) {
     }
 }
 
-const void* stream_kernel(int dtype, int cpl) {
+template <bool UPD>
+const void* stream_kernel_t(int dtype, int cpl) {
     const bool f64 = dtype == CSK_F64;
     switch (cpl) {
-        case 1: return f64 ? (const void*)k_iterate_gemv_stream<double, 1> : (const void*)k_iterate_gemv_stream<float, 1>;
-        case 2: return f64 ? (const void*)k_iterate_gemv_stream<double, 2> : (const void*)k_iterate_gemv_stream<float, 2>;
-        case 4: return f64 ? (const void*)k_iterate_gemv_stream<double, 4> : (const void*)k_iterate_gemv_stream<float, 4>;
-        case 8: return f64 ? (const void*)k_iterate_gemv_stream<double, 8> : (const void*)k_iterate_gemv_stream<float, 8>;
+        case 1: return f64 ? (const void*)k_iterate_gemv_stream<double, 1, UPD> : (const void*)k_iterate_gemv_stream<float, 1, UPD>;
+        case 2: return f64 ? (const void*)k_iterate_gemv_stream<double, 2, UPD> : (const void*)k_iterate_gemv_stream<float, 2, UPD>;
+        case 4: return f64 ? (const void*)k_iterate_gemv_stream<double, 4, UPD> : (const void*)k_iterate_gemv_stream<float, 4, UPD>;
+        case 8: return f64 ? (const void*)k_iterate_gemv_stream<double, 8, UPD> : (const void*)k_iterate_gemv_stream<float, 8, UPD>;
         default: return nullptr;
     }
+}
+
+const void* stream_kernel(int dtype, int cpl, bool upd) {
+    return upd ? stream_kernel_t<true>(dtype, cpl) : stream_kernel_t<false>(dtype, cpl);
 }
 
 int stream_rows_per_block(int dtype, int cpl) {
@@ -1155,17 +1184,21 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
     }
     if (variant == 2 && cfg->reg_rpw == 0) return CSK_EUNSUPPORTED;
     // rows streamed through a bulk-copy ring: on request, or when the rows
-    // stay resident neither in registers nor in shared memory
+    // stay resident neither in registers nor in shared memory; the
+    // residual-update form (Remark 1) always runs this loop
     cfg->stream_cpl = 0;
     const int vlen = 16 / s;                 // elements per 16-byte chunk
-    if (path == CSK_RESID_GEMV && vec_ok && n % vlen == 0 &&
-        (variant == 3 || (variant == 0 && cfg->reg_rpw == 0 && !cfg->cache_rows))) {
+    const bool upd = path == CSK_RESID_UPDATE;
+    if (upd) cfg->reg_rpw = cfg->reg_cpl = 0;
+    if ((upd || path == CSK_RESID_GEMV) && vec_ok && n % vlen == 0 &&
+        (upd || variant == 3 || (variant == 0 && cfg->reg_rpw == 0 && !cfg->cache_rows))) {
         const int need_c = (n / vlen + 31) / 32;
         const int cpl = need_c <= 1 ? 1 : need_c <= 2 ? 2 : need_c <= 4 ? 4 : need_c <= 8 ? 8 : 0;
         int nst = kMaxStreamStages;
-        while (cpl && nst > 2 && stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst) > budget)
+        while (cpl && nst > 2 &&
+               stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst, upd) > budget)
             --nst;
-        const size_t sm = cpl ? stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst) : 0;
+        const size_t sm = cpl ? stream_smem_bytes(R, n, s, stream_rows_per_block(dtype, cpl), nst, upd) : 0;
         if (cpl && sm <= budget) {
             cfg->stream_cpl = cpl;
             cfg->stream_stages = nst;
@@ -1174,7 +1207,7 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
             cfg->smem = sm;
         }
     }
-    if (variant == 3 && cfg->stream_cpl == 0) return CSK_EUNSUPPORTED;
+    if ((variant == 3 || upd) && cfg->stream_cpl == 0) return CSK_EUNSUPPORTED;
     if (cfg->smem > budget) return CSK_EUNSUPPORTED;
     return CSK_OK;
 }
@@ -1184,7 +1217,8 @@ cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg
     const bool reg = cfg.reg_rpw > 0;
     const bool stream = cfg.stream_cpl > 0;
     if (path == CSK_RESID_GRAM) fn = (void*)k_iterate_gram;
-    else if (stream) fn = const_cast<void*>(stream_kernel(p.dtype, cfg.stream_cpl));
+    else if (stream) fn = const_cast<void*>(stream_kernel(p.dtype, cfg.stream_cpl,
+                                                          path == CSK_RESID_UPDATE));
     else if (reg) fn = const_cast<void*>(reg_kernel(cfg.reg_rpw, cfg.reg_cpl));
     else fn = const_cast<void*>(gemv_kernel(p.dtype, cfg.rows_per_cta));
     if (!fn) return cudaErrorInvalidValue;

@@ -527,7 +527,8 @@ k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __rest
 
 // --------------------------------------------- bucket-owner sketch (FP32)
 // FP32 sketches whose buckets are small (at most kOwnMaxMean rows on
-// average, d <= 65535) skip the global counting sort.  k_hash16 stores every
+// average, d <= 65535) and whose A is at most kOwnMaxElems elements skip the
+// global counting sort.  k_hash16 stores every
 // row's bucket h(i) in 16 bits; then CTA b of k_sketch_own owns the
 // contiguous buckets [d b / G, d (b + 1) / G) and does everything for them:
 //   1. scans h (16-byte loads, L2-resident): counts the rows of every owned
@@ -550,6 +551,7 @@ constexpr int kOwnThreads = 512;
 constexpr int kOwnWarps = kOwnThreads / 32;
 constexpr int kOwnMaxBuckets = 1024;      // buckets one CTA owns at most
 constexpr int kOwnMaxMean = 128;          // mean rows per bucket of this path
+constexpr int64_t kOwnMaxElems = 32ll << 20;   // elements of A of this path (by default)
 constexpr int kOwnMaxCap = 16384;         // rows a CTA lists in shared memory at most
 
 __global__ void k_hash16(int64_t m, uint32_t d, uint64_t seed, uint16_t* __restrict__ h) {
@@ -710,18 +712,16 @@ k_sketch_own(const float* __restrict__ A, int64_t lda, int n, int64_t m,
     __syncthreads();
     pdl_wait();                         // h comes from the hash pass
 
-    // 1. count (and list) the owned rows; rows of earlier buckets give the offset
+    // 1. count (and list) the owned rows; rows of earlier buckets give the offset.
+    // Each thread issues kScanLoads 16-byte loads before looking at any, so a
+    // CTA's scan of h costs a few L2 round trips, not one per load.
+    constexpr int kScanLoads = 8;
     int below = 0;
-    for (int64_t i0 = (int64_t)tid * 8; i0 < m; i0 += (int64_t)kOwnThreads * 8) {
-        uint16_t v[8];
-        if (i0 + 8 <= m) {
-            const uint4 t = __ldg(reinterpret_cast<const uint4*>(h + i0));
-            v[0] = t.x & 0xFFFF; v[1] = t.x >> 16; v[2] = t.y & 0xFFFF; v[3] = t.y >> 16;
-            v[4] = t.z & 0xFFFF; v[5] = t.z >> 16; v[6] = t.w & 0xFFFF; v[7] = t.w >> 16;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = i0 + q < m ? h[i0 + q] : (uint16_t)0xFFFF;
-        }
+    auto take = [&](int64_t i0, const uint4& t) {
+        const uint16_t v[8] = {(uint16_t)(t.x & 0xFFFF), (uint16_t)(t.x >> 16),
+                               (uint16_t)(t.y & 0xFFFF), (uint16_t)(t.y >> 16),
+                               (uint16_t)(t.z & 0xFFFF), (uint16_t)(t.z >> 16),
+                               (uint16_t)(t.w & 0xFFFF), (uint16_t)(t.w >> 16)};
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int hv = v[q];               // 0xFFFF is no bucket: d <= 65535
@@ -733,6 +733,25 @@ k_sketch_own(const float* __restrict__ A, int64_t lda, int n, int64_t m,
                 if (p < cap) list[p] = (int32_t)(i0 + q);
             }
         }
+    };
+    const int64_t m8 = m / 8;                  // whole 16-byte groups
+    const uint4* h4 = reinterpret_cast<const uint4*>(h);
+    for (int64_t g0 = tid; g0 < m8; g0 += (int64_t)kOwnThreads * kScanLoads) {
+        uint4 t[kScanLoads];
+#pragma unroll
+        for (int u = 0; u < kScanLoads; ++u) {
+            const int64_t g = g0 + (int64_t)u * kOwnThreads;
+            t[u] = g < m8 ? __ldg(h4 + g) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu,
+                                                       0xFFFFFFFFu);
+        }
+#pragma unroll
+        for (int u = 0; u < kScanLoads; ++u) take((g0 + (int64_t)u * kOwnThreads) * 8, t[u]);
+    }
+    if (tid == 0 && m8 * 8 < m) {              // the last m % 8 rows
+        uint16_t v[8];
+        for (int q = 0; q < 8; ++q) v[q] = m8 * 8 + q < m ? h[m8 * 8 + q] : (uint16_t)0xFFFF;
+        take(m8 * 8, make_uint4(v[0] | ((uint32_t)v[1] << 16), v[2] | ((uint32_t)v[3] << 16),
+                                v[4] | ((uint32_t)v[5] << 16), v[6] | ((uint32_t)v[7] << 16)));
     }
     below = warp_sum(below);
     if (lane == 0) sh.below_w[warp] = below;
@@ -1036,12 +1055,15 @@ int sketch_path_override() {
     return p;
 }
 
-bool use_owner_path(int dtype, int64_t m, int64_t d) {
+bool use_owner_path(int dtype, int64_t m, int64_t n, int64_t d) {
     if (dtype != CSK_F32 || d > 65535 || m > (int64_t)INT_MAX / 2) return false;
     const int o = sketch_path_override();
     if (o == 1) return false;
     if (o == 2) return true;
-    return m <= (int64_t)kOwnMaxMean * d;
+    // measured on GB300: ahead of the counting sort up to ~25M elements of A
+    // (fixed costs of the sort chain dominate there), behind it at
+    // 100000 x 500 with one right-hand side and above
+    return m <= (int64_t)kOwnMaxMean * d && m * (int64_t)n <= kOwnMaxElems;
 }
 
 cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, const float* B,
@@ -1056,8 +1078,9 @@ cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, con
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
-    // CTAs: one per SM (16 warps, 8 16-byte loads in flight per lane), at
-    // least ceil(d / kOwnMaxBuckets), at most d
+    // CTAs: one per SM (16 warps, 8 16-byte loads in flight per lane; two
+    // 256-thread CTAs per SM measured slower), at least ceil(d /
+    // kOwnMaxBuckets), at most d
     int64_t G = di.sms;
     const int64_t gmin = ((int64_t)d + kOwnMaxBuckets - 1) / kOwnMaxBuckets;
     if (G < gmin) G = gmin;
@@ -1097,7 +1120,7 @@ cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, con
 cudaError_t launch_sketch(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
                           int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
                           void* At, void* Bt, double* N2, cudaStream_t st) {
-    if (use_owner_path(dtype, m, d))
+    if (use_owner_path(dtype, m, n, d))
         return launch_sketch_own(static_cast<const float*>(A), lda, m, n,
                                  nrhs > 0 ? static_cast<const float*>(B) : nullptr, ldb, nrhs, s, d,
                                  seed, static_cast<float*>(At), static_cast<float*>(Bt), N2, st);

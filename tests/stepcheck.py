@@ -33,6 +33,11 @@ Bounds on the residual the GPU scores (u = 2^-24, the FP32 unit roundoff):
   with S = |At| |At_{i_k}|^T and |alpha_k| <= (|r_{k,i_k}| + B_{k,i_k}) /
   ||At_{i_k}||^2 (1 + 4u).  The bound grows with the drift since the last
   refresh, which is what it has to cover.
+* UPDATE path (the residual-update form of Remark 1: r_{k+1} = r_k - alpha_k
+  fl(At At_{i_k}^T), r_{i_k} := 0, recomputed as bt - At x in the working
+  precision at step 0 and every K steps): the GRAM recursion with c_G
+  replaced by gamma_n, the error of each dot product At_j . At_{i_k}, and the
+  GEMV bound at the recomputation steps.
 """
 from __future__ import annotations
 
@@ -87,10 +92,12 @@ def replay(At, bt, X, ik, steps, path="gemv", refresh=0, u=U32, name="", oracle=
            oracle_steps=None, nthreads=8, block=256) -> StepReport:
     """Check `steps` GPU steps (needs X[0..steps] and ik[0..steps-1]).
 
-    path: "gemv" (residual recomputed every step) or "gram" (updated with
+    path: "gemv" (residual recomputed every step), "gram" (updated with
     the split-BF16 Gram matrix, FP64 recomputation at steps 0, K, 2K, ... for
     refresh = K > 0, at step 0 only for refresh = 0 -- the batched loop with
-    x0 = 0 starts from r = bt exactly, which the refresh formula covers).
+    x0 = 0 starts from r = bt exactly, which the refresh formula covers) or
+    "update" (updated with dot products against the chosen row, recomputed in
+    the working precision at steps 0, K, 2K, ...).
     oracle: the oracle module, to run its own selection from each x_k at the
     steps `oracle_steps` (default: all).  The residuals of a block of steps
     are formed with one matrix product."""
@@ -105,22 +112,23 @@ def replay(At, bt, X, ik, steps, path="gemv", refresh=0, u=U32, name="", oracle=
     rep = StepReport(name or path)
     g = (n + 1) * u / (1 - (n + 1) * u)
     g64 = (n + 2) * U64
-    cg = split_bf16_coeff(n)
+    cg = split_bf16_coeff(n) if path == "gram" else n * u / (1 - n * u)
     B = None
     for k0 in range(0, steps, block):
         k1 = min(steps, k0 + block)
         Rb = b[:, None] - A @ Xd[k0:k1 + 1].T          # r at x_k0 .. x_k1
         Pb = absA @ np.abs(Xd[k0:k1 + 1]).T
-        Sb = absA @ absA[ik[k0:k1]].T if path == "gram" else None
+        Sb = absA @ absA[ik[k0:k1]].T if path in ("gram", "update") else None
         for k in range(k0, k1):
             q = k - k0
             x, x1 = Xd[k], Xd[k + 1]
             R, P = Rb[:, q], Pb[:, q]
-            if path == "gemv":
+            fresh = k == 0 or (refresh > 0 and k % refresh == 0)
+            if path == "gemv" or (path == "update" and fresh):
                 B = g * (np.abs(b) + P)
-            elif k == 0 or (refresh > 0 and k % refresh == 0):
+            elif fresh:
                 B = u * np.abs(R) + 2 * g64 * P
-            # (gram: B carried over from the previous step otherwise)
+            # (gram, update: B carried over from the previous step otherwise)
             j = int(ik[k])
             assert 0 <= j < d and valid[j], (name, k, j)
             hi, lo = _keys(R, B, N, valid, u)
@@ -146,7 +154,7 @@ def replay(At, bt, X, ik, steps, path="gemv", refresh=0, u=U32, name="", oracle=
                 else:
                     # a different pick is allowed only where both rows are admissible
                     assert not forced_o and hi[jo] >= lo.max(), (name, "oracle pick", k, j, jo)
-            if path == "gram":
+            if path in ("gram", "update"):
                 R1, P1 = Rb[:, q + 1], Pb[:, q + 1]
                 amax = (abs(R[j]) + B[j]) / N[j] * (1 + 4 * u)
                 drift = amax * cg * Sb[:, q]

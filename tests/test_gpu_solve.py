@@ -435,3 +435,57 @@ def test_inconsistent_system_residual_stop_fp32(csk):
     assert floor * (1 - 1e-6) <= info["resid"] ** 2 <= tol * (1 + 1e-3)
     assert abs(info["iters"] - ref.iters) <= max(2, 0.02 * ref.iters)
     _compare_prefix(ik.cpu().numpy(), ref, 1e-3)
+
+
+@pytest.mark.parametrize("dt,refresh", [(np.float32, 0), (np.float32, 40), (np.float64, 0)])
+def test_residual_update_form_unsketched_mwrk(csk, dt, refresh):
+    """Remark 1's residual-update form of MWRK on A itself (d = 0): the loop
+    keeps r and subtracts alpha A A_{i_k}^T each step (a GEMV of A against
+    the chosen row), recomputing bt - A x every `refresh` steps.  RES <= 1e-6
+    at the oracle's IT (+-2 %), and every step replayed from the GPU's own
+    iterate within the update form's bound (rounding of the dot products
+    against the chosen row accumulated since the last recomputation), with
+    the oracle's selection from the same iterate."""
+    m, n, seed = 30000, 120, 21
+    s = synth.gaussian_system(m, n, seed, dt)
+    u = 2.0 ** -24 if dt == np.float32 else 2.0 ** -53
+    A = _to(s.A)
+    ik = torch.full((20000,), -1, dtype=torch.int32, device=DEV)
+    X = torch.zeros((20000, n), dtype=A.dtype, device=DEV)
+    p = csk.csk_params_default(d=0, path=csk.UPDATE, refresh_every=refresh, ik_log=ik.data_ptr(),
+                               ik_log_len=20000, x_log=X.data_ptr(), x_log_len=20000)
+    x, info = csk.csk_solve(A, _to(s.b), p, x_star=_to(s.x_star.astype(dt)))
+    ref = oracle.mwrk(s.A.astype(np.float64), s.b.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and info["rse"] <= 1e-6 and info["path"] == csk.UPDATE
+    assert abs(info["iters"] - ref.iters) <= max(2, 0.02 * ref.iters)
+    steps = info["iters"]
+    ikh = ik.cpu().numpy()
+    Xh = np.concatenate([X.cpu().numpy()[:steps], x.cpu().numpy()[None]])
+    name = f"{'FP32' if dt == np.float32 else 'FP64'} residual-update MWRK {m}x{n} refresh {refresh}"
+    rep = stepcheck.replay(s.A, s.b, Xh, ikh, steps, path="update", refresh=refresh, u=u,
+                           name=name, oracle=oracle)
+    rep.prefix, _ = stepcheck.trajectory_prefix(ikh, ref, 1e-3 if dt == np.float32 else 1e-9)
+    stepcheck.record(rep)
+    assert rep.steps == steps and rep.oracle_equal >= 0.9 * steps
+
+
+def test_residual_update_form_sketched_fp32(csk):
+    """The residual-update form on a sketch (100000 x 500 FP32, d = 5000):
+    the same replay, and the same IT as the GEMV form within 2 %."""
+    m, n, d, seed = 100000, 500, 5000, 0
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x, info, ik, X = _solve(csk, s, d, seed, log=20000, xlog=20000, path=csk.UPDATE,
+                            refresh_every=100)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+    _, info_g, _ = _solve(csk, s, d, seed, path=csk.GEMV)
+    assert abs(info["iters"] - info_g["iters"]) <= 0.02 * info_g["iters"]
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    steps = info["iters"]
+    Xh = np.concatenate([X[:steps], x[None]])
+    rep = stepcheck.replay(At32, bt32, Xh, ik, steps, path="update", refresh=100,
+                           name="FP32 residual-update CSK 100000x500 d=5000 refresh 100",
+                           oracle=oracle)
+    stepcheck.record(rep)
+    assert rep.steps == steps and rep.oracle_equal >= 0.9 * steps
