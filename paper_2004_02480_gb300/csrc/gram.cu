@@ -25,6 +25,8 @@
 // K loop: 3 segments of ceil(n/64) chunks: (hi, hi), (hi, lo), (lo, hi).
 // Every mbarrier wait is bounded; on expiry the CTA records CSK_ETIMEOUT,
 // drains its own TMA loads (bounded), frees its TMEM and returns.
+#include <cstdlib>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -69,6 +71,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "l"(policy)
         : "memory");
 }
+// The same load multicast to the CTAs of `mask` in the cluster: the box lands
+// at the same shared-memory offset in each and completes its bytes on the
+// mbarrier at the same offset there.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                               int c0, int c1, uint16_t mask, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5, %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "h"(mask), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -88,6 +110,14 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      bar)
                  : "memory");
+}
+// Completion of this CTA's MMAs arrives on the mbarrier at the same offset in
+// every CTA of `mask` (both CTAs of a pair release a stage they share).
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
@@ -139,6 +169,30 @@ __device__ __forceinline__ bool tile_at(int t, int nbi, int nbj, int* bi, int* b
     return *bi < nbi && (*bj * BN + BN - 1) >= (*bi * BM);
 }
 
+// Pair order: the two CTAs of a cluster take row blocks 2p and 2p + 1 of the
+// same column block bj (they share its B panel); pairs are grouped like the
+// row blocks above.  A pair is skipped when both tiles lie below the
+// diagonal (the even one has the larger part above it).
+constexpr int kGroupPairs = kGroupRows / 2;
+
+__device__ __forceinline__ bool pair_at(int t, int npairs, int nbj, int* p, int* bj) {
+    const int per_group = kGroupPairs * nbj;
+    const int g = t / per_group, rem = t - g * per_group;
+    *bj = rem / kGroupPairs;
+    *p = g * kGroupPairs + (rem - *bj * kGroupPairs);
+    return *p < npairs && (*bj * BN + BN - 1) >= (2 * *p * BM);
+}
+
+// Tile t of this CTA's sequence: (bi, bj), or false to skip it.
+template <bool PAIR>
+__device__ __forceinline__ bool tile_of(int t, int nbi, int nbj, uint32_t rank, int* bi, int* bj) {
+    if (!PAIR) return tile_at(t, nbi, nbj, bi, bj);
+    int p;
+    if (!pair_at(t, nbi / 2, nbj, &p, bj)) return false;
+    *bi = 2 * p + (int)rank;
+    return true;
+}
+
 // ----------------------------------------------------------------- kernels
 __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_pad, int k_pad,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
@@ -158,6 +212,16 @@ __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_p
 // one of two TMEM accumulators; warps 2-5 drain the other accumulator to
 // global memory, so a tile's epilogue overlaps the next tile's MMAs.
 // Element (r, c) is written, with its mirror (c, r), exactly when c >= r.
+//
+// PAIR: launched in clusters of two CTAs that take the tiles (2p, bj) and
+// (2p + 1, bj) together.  Each loads its own A panel and half of the shared
+// B panel (128 of its 256 rows), multicast into both CTAs' stage, so a stage
+// costs each SM 32 KB of L2 reads instead of 48 KB; each CTA's stage barrier
+// expects all 48 KB, and a stage is refilled only after both CTAs' MMAs
+// released it (their commits arrive on both CTAs' empty barriers, count 2).
+// Cluster barriers after set-up and before exit keep each CTA resident while
+// its peer may still write into its shared memory.
+template <bool PAIR>
 __global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ CUtensorMap map_lo_a,
           const __grid_constant__ CUtensorMap map_hi_b, const __grid_constant__ CUtensorMap map_lo_b,
@@ -175,7 +239,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; ++st) {
             mbar_init(smem_u32(&full_bar[st]), 1);
-            mbar_init(smem_u32(&empty_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), PAIR ? 2 : 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&acc_full[a]), 1);
@@ -195,8 +259,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (PAIR) cluster_sync_all();          // both CTAs' barriers exist before any load
     const uint32_t tmem = tmem_base_sh;
     const int nch = 3 * kchunks;
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const int first = PAIR ? (int)blockIdx.x / 2 : (int)blockIdx.x;
+    const int step = PAIR ? (int)gridDim.x / 2 : (int)gridDim.x;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -205,9 +273,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             int64_t g = 0;                 // chunk counter over all tiles of this CTA
             int64_t issued = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = first; t < ntiles && ok; t += step) {
                 int bi, bj;
-                if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+                if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
                 for (int c = 0; c < nch; ++c, ++g) {
                     const int st = (int)(g % STAGES);
                     const int64_t r = g / STAGES;
@@ -222,7 +290,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     mbar_expect_tx(fb, STAGE_BYTES);
                     tma_load_2d(sa, ma, fb, kc * BK, bi * BM, pol);
-                    tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN, pol);
+                    if (PAIR)
+                        tma_load_2d_mc(sa + A_BYTES + rank * (B_BYTES / 2),
+                                       seg == 1 ? &map_lo_a : &map_hi_a, fb, kc * BK,
+                                       bj * BN + (int)rank * BM, (uint16_t)3, pol);
+                    else
+                        tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN, pol);
                     issued = g + 1;
                 }
             }
@@ -238,9 +311,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             int64_t g = 0;
             int tc = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = first; t < ntiles && ok; t += step) {
                 int bi, bj;
-                if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+                if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
                 const int a = tc & 1, u = tc >> 1;
                 ++tc;
                 if (u > 0 && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)((u - 1) & 1))) {
@@ -262,7 +335,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                     for (int kk = 0; kk < BK / 16; ++kk)
                         tc_mma_bf16(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
                                     kIdesc, (c > 0 || kk > 0) ? 1u : 0u);
-                    tc_commit(smem_u32(&empty_bar[st]));
+                    if (PAIR) tc_commit_mc(smem_u32(&empty_bar[st]), (uint16_t)3);
+                    else tc_commit(smem_u32(&empty_bar[st]));
                 }
                 if (ok) tc_commit(smem_u32(&acc_full[a]));
             }
@@ -273,9 +347,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
         const int quad = warp & 3;
         const bool vec_ok = (ldg % 4 == 0) && (reinterpret_cast<uintptr_t>(G) % 16 == 0);
         int tc = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int t = first; t < ntiles; t += step) {
             int bi, bj;
-            if (!tile_at(t, nbi, nbj, &bi, &bj)) continue;
+            if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
             const int a = tc & 1, u = tc >> 1;
             ++tc;
             const bool ok = mbar_wait(smem_u32(&acc_full[a]), (uint32_t)(u & 1));
@@ -339,6 +413,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                      "r"(TMEM_COLS)
                      : "memory");
     }
+    if (PAIR) cluster_sync_all();          // the peer no longer writes into this CTA
 }
 
 __global__ void k_gram_diag(const double* __restrict__ N2, int d, float* __restrict__ G, int64_t ldg) {
@@ -379,6 +454,17 @@ bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_rows) {
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Pairs of CTAs sharing B panels (the default); CSK_GRAM_PAIR=0 in the
+// environment selects the one-CTA kernel (same products, same bits), for
+// comparisons.
+bool gram_pairs_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("CSK_GRAM_PAIR");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 }  // namespace
 
 int64_t gram_ld(int d) { return round_up(d, 32); }
@@ -402,16 +488,42 @@ cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* 
         !make_map(&mhb, hi, dp, kp, BN) || !make_map(&mlb, lo, dp, kp, BN))
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
-    cudaError_t e = ensure_smem_attr((const void*)k_gram_tc, smem);
-    if (e != cudaSuccess) return e;
-    const int nbi = dp / BM, nbj = dp / BN;
-    // tile slots of the grouped order (some below the diagonal, skipped)
-    const int ntiles = (nbi + kGroupRows - 1) / kGroupRows * kGroupRows * nbj;
-    int valid = 0;
-    for (int i = 0; i < nbi; ++i) valid += nbj - (i * BM) / BN;
-    const int grid = valid < di.sms ? valid : di.sms;
-    k_gram_tc<<<grid, kGramThreads, smem, st>>>(mha, mla, mhb, mlb, d, kp / BK, ntiles, nbi, nbj, G,
-                                                ldg, info);
+    const int nbi = dp / BM, nbj = dp / BN;          // nbi is even (dp is a multiple of BN)
+    cudaError_t e;
+    if (gram_pairs_enabled()) {
+        e = ensure_smem_attr((const void*)k_gram_tc<true>, smem);
+        if (e != cudaSuccess) return e;
+        const int npairs = nbi / 2;
+        const int ntiles = (npairs + kGroupPairs - 1) / kGroupPairs * kGroupPairs * nbj;
+        int valid = 0;
+        for (int q = 0; q < npairs; ++q) valid += nbj - q;
+        const int pairs = valid < di.sms / 2 ? valid : di.sms / 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * pairs));
+        cfg.blockDim = dim3(kGramThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_gram_tc<true>, mha, mla, mhb, mlb, d, kp / BK, ntiles, nbi,
+                               nbj, G, ldg, info);
+        if (e != cudaSuccess) return e;
+    } else {
+        e = ensure_smem_attr((const void*)k_gram_tc<false>, smem);
+        if (e != cudaSuccess) return e;
+        // tile slots of the grouped order (some below the diagonal, skipped)
+        const int ntiles = (nbi + kGroupRows - 1) / kGroupRows * kGroupRows * nbj;
+        int valid = 0;
+        for (int i = 0; i < nbi; ++i) valid += nbj - (i * BM) / BN;
+        const int grid = valid < di.sms ? valid : di.sms;
+        k_gram_tc<false><<<grid, kGramThreads, smem, st>>>(mha, mla, mhb, mlb, d, kp / BK, ntiles,
+                                                           nbi, nbj, G, ldg, info);
+    }
     if (N2) k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
     note_launches(N2 ? 3 : 2);
     return cudaGetLastError();

@@ -190,3 +190,38 @@ def test_precision_form_full_size(csk):
     rep.prefix = K
     stepcheck.record(rep)
     assert rep.steps == 300
+
+
+GRAM_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2004_02480_gb300 import csk
+out = {}
+for d, n in [(300, 70), (1000, 256), (777, 1000), (5000, 130)]:
+    g = torch.Generator(device="cuda:0").manual_seed(d + n)
+    At = torch.randn((d, n), generator=g, device="cuda:0")
+    out[f"{d}x{n}"] = csk.csk_gram(At).cpu().numpy()
+np.savez(sys.argv[2], **out)
+"""
+
+
+def test_gram_pair_kernel_equals_single_cta_kernel(csk, tmp_path):
+    """The paired-CTA Gram kernel (B panels shared by multicast between the
+    two CTAs of a cluster, the default) and the one-CTA kernel
+    (CSK_GRAM_PAIR=0) issue the same MMAs on the same operands: G must be the
+    same bits, including shapes whose last pair holds a tile below the
+    diagonal and ragged d."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = {}
+    for mode in ("1", "0"):
+        f = str(tmp_path / f"g{mode}.npz")
+        r = subprocess.run([sys.executable, "-c", GRAM_CHILD, root, f], capture_output=True,
+                           text=True, timeout=600, env={**os.environ, "CSK_GRAM_PAIR": mode})
+        assert r.returncode == 0, r.stderr[-3000:]
+        files[mode] = np.load(f)
+    for k in files["1"].files:
+        a, b = files["1"][k], files["0"][k]
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), k
