@@ -116,6 +116,18 @@ typedef struct {
                                pair -- indices into the caller's array and
                                the system's columns; ignored by csk_solve   */
     int32_t log_rhs;
+    int32_t fused;          /* csk_solve: 1 = form the sketch inside the loop's
+                               cooperative kernel (each CTA sketches the rows
+                               it owns in the loop; one launch for the sort,
+                               the sums, the norms and the loop): GEMV path,
+                               d <= 65535, at most 1024 rows per CTA, the
+                               shared-memory loop or the register loop with
+                               rows of 257..512 columns; CSK_EUNSUPPORTED
+                               otherwise.  0 = separate
+                               launches.  Stage events [1] and [2] are then
+                               recorded before the loop, which includes the
+                               sketch                                        */
+    int32_t reserved_;
 } csk_params;
 
 /* Outcome of one solve, written by the device (64 bytes). */

@@ -46,7 +46,8 @@ class csk_params(ctypes.Structure):
                 ("x_log", ctypes.c_void_p), ("x_log_len", ctypes.c_int64),
                 ("threads", ctypes.c_int32), ("gemv_variant", ctypes.c_int32),
                 ("stage_events", ctypes.c_void_p * 5), ("log_system", ctypes.c_int32),
-                ("log_rhs", ctypes.c_int32)]
+                ("log_rhs", ctypes.c_int32), ("fused", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 class csk_system(ctypes.Structure):

@@ -43,7 +43,7 @@ __global__ void k_info_init(csk_info* info, int path, int rows, int grid) {
 //   G (d x d, GRAM) | Gram operand scratch (GRAM)
 
 struct SolveLayout {
-    size_t sort, At, bt, N2, norm, slots, xg, part, G, gscr, total;
+    size_t sort, At, bt, N2, norm, slots, xg, part, fpart, G, gscr, total;
 };
 
 void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLayout* L) {
@@ -58,6 +58,7 @@ void solve_layout(int64_t m, int64_t n, int dtype, int64_t d, int path, SolveLay
     L->slots = o; o += align256(exchange_bytes(kMaxIterGrid));
     L->xg = o;    o += align256((size_t)n * s);
     L->part = o;  o += align256(final_check_partials((int)rows) * 8);
+    L->fpart = o; o += align256((size_t)kMaxIterGrid * 8);
     L->G = o;     o += path == CSK_RESID_GRAM ? align256((size_t)rows * gram_ld((int)rows) * 4) : 0;
     L->gscr = o;  o += path == CSK_RESID_GRAM ? align256(gram_scratch_bytes((int)rows, (int)n)) : 0;
     L->total = o;
@@ -82,6 +83,10 @@ int check_solve_args(int64_t m, int64_t n, int64_t lda, int32_t dtype, const csk
     if (params->path < CSK_RESID_GEMV || params->path > CSK_RESID_UPDATE) return CSK_EINVAL;
     if (params->grid < 0 || params->refresh_every < 0) return CSK_EINVAL;
     if (params->gemv_variant < 0 || params->gemv_variant > 3) return CSK_EINVAL;
+    if (params->fused != 0 && params->fused != 1) return CSK_EINVAL;
+    if (params->fused && (params->d == 0 || resolve_path(params->path, dtype, params->d, n) !=
+                                                CSK_RESID_GEMV))
+        return CSK_EUNSUPPORTED;
     if (m > INT_MAX || n > INT_MAX || d > INT_MAX) return CSK_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
     const int path = resolve_path(params->path, dtype, d, n);
@@ -148,9 +153,52 @@ int solve_enqueue(const void* A, int64_t m, int64_t n, int64_t lda, const void* 
     const void* bt;
     int64_t ld;
     double* N2 = reinterpret_cast<double*>(w + L.N2);
+    int fcap = 0;
+    size_t fsmem = 0;
+    if (params->fused) {
+        rc = plan_fused(dtype, m, (int)d, (int)n, cfg, A, lda, &fcap, &fsmem);
+        if (rc != CSK_OK) return rc;
+    }
     record(params, 0, st);
     k_info_init<<<1, 1, 0, st>>>(info, path, rows, cfg.grid);
     note_launches(1);
+    if (params->fused) {
+        // the whole loop, sketch included, in one cooperative kernel
+        Slot* slots = reinterpret_cast<Slot*>(w + L.slots);
+        if (cudaMemsetAsync(slots, 0, exchange_bytes(cfg.grid), st) != cudaSuccess) return CSK_ECUDA;
+        record(params, 1, st);
+        record(params, 2, st);
+        SortScratch s;
+        carve_sort_scratch(w + L.sort, m, d, &s);
+        FusedArgs fa;
+        fa.A = A; fa.lda = lda; fa.m = m; fa.b = b; fa.seed = params->seed;
+        fa.h = reinterpret_cast<uint16_t*>(s.perm_tmp);
+        fa.perm = s.perm;
+        fa.off = s.off;
+        fa.part = reinterpret_cast<double*>(w + L.fpart);
+        IterProblem p;
+        p.dtype = dtype;
+        p.At = w + L.At; p.ld = n; p.d = rows; p.n = (int)n;
+        p.bt = w + L.bt; p.N2 = N2;
+        p.x0 = x0; p.xstar = x_star; p.x_out = x_out;
+        p.stop_norm = nullptr;
+        p.slots = slots;
+        p.xg = w + L.xg;
+        p.G = nullptr; p.ldg = 0;
+        p.refresh_every = params->refresh_every;
+        p.ik_log = params->ik_log; p.ik_log_len = params->ik_log_len;
+        p.x_log = params->x_log; p.x_log_len = params->x_log_len;
+        p.tol = params->tol; p.max_iter = params->max_iter;
+        p.spin_limit = params->spin_limit; p.fault_inject = params->fault_inject;
+        p.info = info;
+        if (launch_fused(dtype, p, cfg, fa, fcap, fsmem, st) != cudaSuccess) return CSK_ECUDA;
+        record(params, 3, st);
+        if (launch_final_check(dtype, w + L.At, n, rows, (int)n, w + L.bt, N2, x_out, x_star,
+                               reinterpret_cast<double*>(w + L.part), info, st) != cudaSuccess)
+            return CSK_ECUDA;
+        record(params, 4, st);
+        return CSK_OK;
+    }
     if (d > 0) {
         SortScratch s;
         carve_sort_scratch(w + L.sort, m, d, &s);

@@ -36,6 +36,7 @@
 #include "common.cuh"
 #include "fp64.cuh"
 #include "kernels.h"
+#include "own_sketch.cuh"
 #include "reduce.cuh"
 
 namespace csk {
@@ -279,9 +280,20 @@ __device__ __forceinline__ double chunk_sq(const double (&t)[2]) {
 
 // ------------------------------------------------------------ GEMV path
 // Shared memory: x (npad) | w2 (Rpad) | bt (Rpad) | x* slice (spad) | At rows
-template <typename T, int NR>
-__global__ void __launch_bounds__(kIterThreads, 1)
-k_iterate_gemv(IterProblem p, int R, int cache_rows) {
+// Loads of rows of At from other CTAs: through the read-only path, except in
+// the fused kernels, where At is written earlier in the same launch (then
+// coherent L2 loads).
+template <bool FUSED, typename V>
+__device__ __forceinline__ V ld_row(const V* q) {
+    if (FUSED) return __ldcg(q);
+    return __ldg(q);
+}
+
+// The loop body; stop_norm is ||x*||^2 (or ||bt||^2 without x*), round0 the
+// exchange round it starts at.
+template <typename T, int NR, bool FUSED>
+__device__ __forceinline__ void gemv_loop(const IterProblem& p, int R, int cache_rows,
+                                          double stop_norm, uint32_t round0) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ RedShared<T> sh;
     int par = 0;
@@ -323,14 +335,14 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
             As[e] = At[(int64_t)(r0 + q) * p.ld + c];
         }
     __syncthreads();
-    const T threshold = (T)(p.tol * *p.stop_norm);   // RES <= tol  <=>  stat <= tol ||x*||^2
+    const T threshold = (T)(p.tol * stop_norm);      // RES <= tol  <=>  stat <= tol ||x*||^2
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     const int64_t lda = cache_rows ? (int64_t)n : p.ld;
     const T* Abase = cache_rows ? As : At + (int64_t)r0 * p.ld;
     // 128-bit row loads: FP32, n % 4 == 0 and 16-byte aligned rows
     const bool vec4 = sizeof(T) == 4 && (n & 3) == 0 && (lda & 3) == 0 &&
                       (reinterpret_cast<uintptr_t>(Abase) & 15) == 0;
-    uint32_t round = 0;
+    uint32_t round = round0;
     int64_t k = 0;
     int status = CSK_OK;
     for (;;) {
@@ -413,7 +425,7 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
             for (int col = tid; col < n; col += blockDim.x) static_cast<T*>(p.x_log)[k * n + col] = xs[col];
         // projection onto row i_k: x += alpha * At_{i_k}^T (same in every CTA)
         const T* arow = At + (int64_t)c.idx * p.ld;
-        for (int col = tid; col < n; col += blockDim.x) xs[col] = fma(c.alpha, __ldg(arow + col), xs[col]);
+        for (int col = tid; col < n; col += blockDim.x) xs[col] = fma(c.alpha, ld_row<FUSED>(arow + col), xs[col]);
         __syncthreads();
         ++k;
     }
@@ -424,6 +436,12 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
     finish(p.info, status, k);
 }
 
+template <typename T, int NR>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_iterate_gemv(IterProblem p, int R, int cache_rows) {
+    gemv_loop<T, NR, false>(p, R, cache_rows, *p.stop_norm, 0);
+}
+
 // ------------------------------------------------ GEMV path, registers
 // FP32 variant for n <= 128 * CPL (n % 4 == 0) and at most kWarps * RPW rows
 // per CTA: warp w keeps rows w, w + kWarps, ... of At in registers (lane l
@@ -432,9 +450,9 @@ k_iterate_gemv(IterProblem p, int R, int cache_rows) {
 // CTA reduction.  The projection is applied by every warp to its own copy
 // of x (identical arithmetic everywhere); float4 column c4 of the
 // ||x - x*||^2 statistic is counted by CTA c4 % grid alone.
-template <int RPW, int CPL>
-__global__ void __launch_bounds__(kIterThreads, 1)
-k_iterate_gemv_reg(IterProblem p, int R) {
+template <int RPW, int CPL, bool FUSED>
+__device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double stop_norm,
+                                         uint32_t round0) {
     __shared__ RedShared<float> sh;
     int par = 0;
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -471,9 +489,9 @@ k_iterate_gemv_reg(IterProblem p, int R) {
         xsr[i] = (xstar && c4 < n4) ? reinterpret_cast<const float4*>(xstar)[c4]
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float threshold = (float)(p.tol * *p.stop_norm);
+    const float threshold = (float)(p.tol * stop_norm);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
-    uint32_t round = 0;
+    uint32_t round = round0;
     int64_t k = 0;
     int status = CSK_OK;
     for (;;) {
@@ -545,7 +563,7 @@ k_iterate_gemv_reg(IterProblem p, int R) {
         for (int i = 0; i < CPL; ++i) {
             const int c4 = lane + 32 * i;
             if (c4 < n4) {
-                const float4 v = __ldg(arow + c4);
+                const float4 v = ld_row<FUSED>(arow + c4);
                 xr[i].x = fmaf(c.alpha, v.x, xr[i].x);
                 xr[i].y = fmaf(c.alpha, v.y, xr[i].y);
                 xr[i].z = fmaf(c.alpha, v.z, xr[i].z);
@@ -563,11 +581,145 @@ k_iterate_gemv_reg(IterProblem p, int R) {
     finish(p.info, status, k);
 }
 
+template <int RPW, int CPL>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_iterate_gemv_reg(IterProblem p, int R) {
+    reg_loop<RPW, CPL, false>(p, R, *p.stop_norm, 0);
+}
+
+// ------------------------------------------- fused sketch and loop
+// One cooperative launch for the whole of Algorithm 1 on a sketch: the CTA
+// that will own rows [r0, r1) of At in the loop first forms them itself.
+//   1. every CTA stores the 16-bit buckets h(i) of a share of the rows
+//      (Definition 1), then one exchange round (acquire) makes them visible;
+//   2. the CTA sketches buckets [r0, r1) exactly as csk_sketch's bucket-owner
+//      kernel does (own_sketch.cuh: rows in ascending order, the same FP
+//      additions), writing At, bt and the FP64 row norms of its rows;
+//   3. the stopping norm: ||x*||^2, computed by every CTA in the same order,
+//      or ||bt||^2 from the CTAs' FP64 partials after a second exchange round
+//      (acquire), which also makes every CTA's rows of At visible to the
+//      projections of the loop;
+//   4. the loop, from exchange round 2 on, reading other CTAs' rows of At
+//      with coherent loads.
+// The sort chain, the segmented sums, the norms and the loop thus run in one
+// kernel; only the status record's initialisation and the FP64 final check
+// are launches of their own.
+struct FusedSketch {
+    const void* A;
+    int64_t lda, m;
+    const void* b;
+    uint64_t seed;
+    uint16_t* h;          // m buckets (scratch)
+    int32_t* perm;        // m (scratch)
+    int32_t* off;         // d + 1 (scratch)
+    double* part;         // one FP64 partial per CTA (scratch)
+    int cap;              // rows a CTA lists in shared memory
+};
+
+__device__ __forceinline__ double block_sum_f64_fixed(double v, double* sh) {
+    v = warp_sum(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += sh[w];     // the same order in every CTA
+    __syncthreads();
+    return t;
+}
+
+// Steps 1-3 above; false (status set) when an exchange round ran out.
+template <typename T, int V, int CPL>
+__device__ __forceinline__ bool fused_prologue(const IterProblem& p, const FusedSketch& f, int R,
+                                               int32_t* smem_rows, double* stop_out,
+                                               uint32_t& round) {
+    __shared__ OwnShared osh;
+    __shared__ RedShared<float> rsh;
+    __shared__ double dsh[32];
+    int par = 0;
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    hash16_range(f.m, (uint32_t)p.d, f.seed, f.h, (int64_t)b * blockDim.x + tid,
+                 (int64_t)G * blockDim.x);
+    __threadfence();
+    __syncthreads();
+    Red<float> z;
+    z.key = -1.0f; z.alpha = 0.0f; z.stat = 0.0f; z.idx = INT_MAX;
+    if (!exchange(p.slots, round, z, spin, p.fault_inject, p.info, rsh, par, true)) return false;
+    ++round;
+    const int r0 = min(p.d, b * R), r1 = min(p.d, r0 + R);
+    T* At = static_cast<T*>(const_cast<void*>(p.At));
+    T* bt = static_cast<T*>(const_cast<void*>(p.bt));
+    double* N2 = const_cast<double*>(p.N2);
+    own_sketch_cta<T, V, CPL>(static_cast<const T*>(f.A), f.lda, p.n, f.m,
+                              static_cast<const T*>(f.b), 1, 1, f.h, p.d, f.seed, f.cap, At, bt,
+                              N2, f.perm, f.off, r0, r1, smem_rows, smem_rows + f.cap, osh);
+    __syncthreads();
+    const T* xstar = static_cast<const T*>(p.xstar);
+    double sq = 0.0;
+    if (xstar) {
+        for (int c = tid; c < p.n; c += blockDim.x) sq += (double)xstar[c] * (double)xstar[c];
+    } else {
+        for (int q = r0 + tid; q < r1; q += blockDim.x) sq += (double)bt[q] * (double)bt[q];
+    }
+    sq = block_sum_f64_fixed(sq, dsh);
+    if (!xstar && tid == 0) f.part[b] = sq;
+    __threadfence();
+    __syncthreads();
+    z.key = -1.0f; z.alpha = 0.0f; z.stat = 0.0f; z.idx = INT_MAX;
+    if (!exchange(p.slots, round, z, spin, p.fault_inject, p.info, rsh, par, true)) return false;
+    ++round;
+    if (!xstar) {
+        sq = 0.0;
+        for (int q = 0; q < G; ++q) sq += __ldcg(f.part + q);    // the same order in every CTA
+    }
+    *stop_out = sq;
+    __syncthreads();
+    return true;
+}
+
+template <typename T, int NR, int V, int CPL>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_fused_gemv(IterProblem p, FusedSketch f, int R, int cache_rows) {
+    extern __shared__ __align__(128) unsigned char dsm_f[];
+    uint32_t round = 0;
+    double stop = 0.0;
+    if (!fused_prologue<T, V, CPL>(p, f, R, reinterpret_cast<int32_t*>(dsm_f), &stop, round)) {
+        finish(p.info, CSK_ETIMEOUT, 0);
+        return;
+    }
+    gemv_loop<T, NR, true>(p, R, cache_rows, stop, round);
+}
+
+template <int RPW, int CPL>
+__global__ void __launch_bounds__(kIterThreads, 1)
+k_fused_reg(IterProblem p, FusedSketch f, int R) {
+    extern __shared__ __align__(128) unsigned char dsm_f[];
+    uint32_t round = 0;
+    double stop = 0.0;
+    if (!fused_prologue<float, 4, 4>(p, f, R, reinterpret_cast<int32_t*>(dsm_f), &stop, round)) {
+        finish(p.info, CSK_ETIMEOUT, 0);
+        return;
+    }
+    reg_loop<RPW, CPL, true>(p, R, stop, round);
+}
+
 // Register-resident variants: (rows per warp, float4 per lane per row).
 #define CSK_REG_VARIANTS(X) \
     X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(6, 1) X(8, 1) \
     X(1, 2) X(2, 2) X(3, 2) X(4, 2) X(6, 2) X(8, 2) \
     X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4)
+
+// Fused register loops for rows of 257..512 columns (4 float4 per lane).
+#define CSK_FUSED_REG_VARIANTS(X) X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4)
+
+const void* fused_reg_kernel(int rpw, int cpl) {
+#define CSK_PICK(RPWv, CPLv) \
+    if (rpw == RPWv && cpl == CPLv) return (const void*)k_fused_reg<RPWv, CPLv>;
+    CSK_FUSED_REG_VARIANTS(CSK_PICK)
+#undef CSK_PICK
+    return nullptr;
+}
 
 const void* reg_kernel(int rpw, int cpl) {
 #define CSK_PICK(RPWv, CPLv) \
@@ -892,6 +1044,21 @@ const void* stream_kernel_t(int dtype, int cpl) {
         case 8: return f64 ? (const void*)k_iterate_gemv_stream<double, 8, UPD> : (const void*)k_iterate_gemv_stream<float, 8, UPD>;
         default: return nullptr;
     }
+}
+
+// Fused kernel of the shared-memory GEMV loop; vec: 16-byte loads of A in
+// the sketch (A 16-byte aligned, n and lda multiples of the vector).
+const void* fused_gemv_kernel(int dtype, int rows_per_cta, bool vec) {
+    const int rpw = (rows_per_cta + kWarps - 1) / kWarps;
+    const int nr = rpw <= 1 ? 1 : rpw <= 2 ? 2 : rpw <= 4 ? 4 : kRowsPerWarp;
+#define CSK_F(T, NR) (vec ? (const void*)k_fused_gemv<T, NR, (sizeof(T) == 8 ? 2 : 4), (sizeof(T) == 8 ? 2 : 4)> \
+                         : (const void*)k_fused_gemv<T, NR, 1, 4>)
+    if (dtype == CSK_F64)
+        return nr == 1 ? CSK_F(double, 1) : nr == 2 ? CSK_F(double, 2) : nr == 4 ? CSK_F(double, 4)
+                                                                         : CSK_F(double, 8);
+    return nr == 1 ? CSK_F(float, 1) : nr == 2 ? CSK_F(float, 2) : nr == 4 ? CSK_F(float, 4)
+                                                                   : CSK_F(float, 8);
+#undef CSK_F
 }
 
 const void* stream_kernel(int dtype, int cpl, bool upd) {
@@ -1254,6 +1421,57 @@ cudaError_t launch_exchange_probe(int grid, int64_t rounds, Slot* slots, csk_inf
     if ((int64_t)per_sm * di.sms < grid) return cudaErrorCooperativeLaunchTooLarge;
     void* args[] = {&slots, &rounds, &info};
     e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kIterThreads), args, 0, st);
+    if (e == cudaSuccess) note_launches(1);
+    return e;
+}
+
+int plan_fused(int dtype, int64_t m, int d, int n, const IterConfig& cfg, const void* A,
+               int64_t lda, int* cap, size_t* smem) {
+    if (d > 65535 || m > (int64_t)INT_MAX / 2) return CSK_EUNSUPPORTED;
+    if (cfg.stream_cpl > 0 || cfg.rows_per_cta > kOwnMaxBuckets) return CSK_EUNSUPPORTED;
+    DevInfo di;
+    if (dev_info(&di) != 0) return CSK_ECUDA;
+    const int vl = dtype == CSK_F64 ? 2 : 4;
+    const bool vec = reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % vl == 0 && n % vl == 0;
+    if (cfg.reg_rpw > 0 && (!vec || cfg.reg_cpl != 4)) return CSK_EUNSUPPORTED;
+    // row lists: 1.5 x the mean rows per CTA, within the shared memory left
+    const size_t budget = (size_t)di.smem_optin - 2048 - sizeof(OwnShared);
+    int64_t c = (3 * (m / cfg.grid) / 2 + 511) / 256 * 256;
+    if (c < 1024) c = 1024;
+    if (c > 16384) c = 16384;
+    while (c > 256 && (size_t)c * 8 > budget) c -= 256;
+    *cap = (int)c;
+    *smem = cfg.smem > (size_t)c * 8 ? cfg.smem : (size_t)c * 8;
+    if (*smem > budget) return CSK_EUNSUPPORTED;
+    return CSK_OK;
+}
+
+cudaError_t launch_fused(int dtype, const IterProblem& p, const IterConfig& cfg,
+                         const FusedArgs& fa, int cap, size_t smem, cudaStream_t st) {
+    const int vl = dtype == CSK_F64 ? 2 : 4;
+    const bool vec = reinterpret_cast<uintptr_t>(fa.A) % 16 == 0 && fa.lda % vl == 0 &&
+                     p.n % vl == 0;
+    const bool reg = cfg.reg_rpw > 0;
+    void* fn = const_cast<void*>(reg ? fused_reg_kernel(cfg.reg_rpw, cfg.reg_cpl)
+                                     : fused_gemv_kernel(dtype, cfg.rows_per_cta, vec));
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_smem_attr(fn, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cached_occupancy(fn, cfg.threads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    DevInfo di;
+    dev_info(&di);
+    if ((int64_t)per_sm * di.sms < cfg.grid) return cudaErrorCooperativeLaunchTooLarge;
+    IterProblem pc = p;
+    FusedSketch f;
+    f.A = fa.A; f.lda = fa.lda; f.m = fa.m; f.b = fa.b; f.seed = fa.seed;
+    f.h = fa.h; f.perm = fa.perm; f.off = fa.off; f.part = fa.part; f.cap = cap;
+    int R = cfg.rows_per_cta, cache = cfg.cache_rows;
+    void* args_reg[] = {&pc, &f, &R};
+    void* args_gemv[] = {&pc, &f, &R, &cache};
+    e = cudaLaunchCooperativeKernel(fn, dim3(cfg.grid), dim3(cfg.threads), reg ? args_reg : args_gemv,
+                                    smem, st);
     if (e == cudaSuccess) note_launches(1);
     return e;
 }

@@ -110,6 +110,25 @@ int plan_iterate(int path, int dtype, int d, int n, int grid_req, int variant, b
                  IterConfig* cfg);
 cudaError_t launch_iterate(int path, const IterProblem& p, const IterConfig& cfg, cudaStream_t st);
 
+// The fused sketch-and-loop launch (GEMV path, register or shared-memory
+// loop, d <= 65535): the sketch of A is formed inside the loop's cooperative
+// kernel, each CTA sketching the rows it then owns.  h / perm / off are sort
+// scratch, part one double per CTA.
+struct FusedArgs {
+    const void* A;
+    int64_t lda, m;
+    const void* b;
+    uint64_t seed;
+    uint16_t* h;
+    int32_t* perm;
+    int32_t* off;
+    double* part;
+};
+int plan_fused(int dtype, int64_t m, int d, int n, const IterConfig& cfg, const void* A,
+               int64_t lda, int* cap, size_t* smem);
+cudaError_t launch_fused(int dtype, const IterProblem& p, const IterConfig& cfg,
+                         const FusedArgs& fa, int cap, size_t smem, cudaStream_t st);
+
 // Exchange-only loop of `grid` CTAs for `rounds` rounds (csk_exchange_floor).
 cudaError_t launch_exchange_probe(int grid, int64_t rounds, Slot* slots, csk_info* info,
                                   cudaStream_t st);

@@ -489,3 +489,73 @@ def test_residual_update_form_sketched_fp32(csk):
                            oracle=oracle)
     stepcheck.record(rep)
     assert rep.steps == steps and rep.oracle_equal >= 0.9 * steps
+
+
+def test_fused_launch_fp32_bench_workload(csk):
+    """fused = 1: the sketch (16-bit buckets, each CTA ordering and summing
+    the rows it then owns) and the loop in one cooperative kernel, on the
+    100000 x 500 FP32, d = 5000 workload.  Every step replayed from the GPU's
+    own iterate against the oracle's FP32 same-order sketch (so a sketch
+    that differed from it would show as steps outside the bound), the
+    oracle's selection from the same iterate, IT within 2 % of the FP64
+    oracle's and of the separate-launch solve."""
+    m, n, d, seed = 100000, 500, 5000, 0
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x, info, ik, X = _solve(csk, s, d, seed, log=20000, xlog=20000, path=csk.GEMV, fused=1)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
+    _, info_sep, _ = _solve(csk, s, d, seed, path=csk.GEMV, grid=info["grid"])
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At32.astype(np.float64), bt32.astype(np.float64), x_star=s.x_star,
+                      tol=1e-6, log_len=20000, nthreads=8)
+    assert abs(info["iters"] - ref.iters) <= 0.02 * ref.iters
+    assert abs(info["iters"] - info_sep["iters"]) <= 0.02 * info_sep["iters"]
+    steps = info["iters"]
+    Xh = np.concatenate([X[:steps], x[None]])
+    assert _check_steps(At32, bt32, Xh, ik, steps, 2.0 ** -24,
+                        name="FP32 fused launch 100000x500 d=5000") == steps
+    xs32 = s.x_star.astype(np.float32).astype(np.float64)      # the x* the GPU was given
+    rse, res = oracle.final_check(At32.astype(np.float64), bt32.astype(np.float64), x, xs32)
+    assert abs(info["rse"] - rse) <= 1e-9 * rse and abs(info["resid"] - res) <= 1e-6 * res
+
+
+@pytest.mark.parametrize("m,n,d,seed", [(2000, 50, 500, 0), (300000, 50, 2500, 1),
+                                        (300000, 100, 10000, 2)])
+def test_fused_launch_fp64_matches_oracle(csk, m, n, d, seed):
+    """fused = 1 in FP64 (the 2000 x 50 workload and Table 1 shapes, d = n^2,
+    shared-memory loop): the sketch is the oracle's bit for bit (same
+    ascending-order additions), so the row sequence must equal the oracle's
+    wherever the selection gap exceeds 1e-9, with the oracle's IT and an x
+    within FP64 rounding of the oracle's."""
+    s = synth.gaussian_system(m, n, seed, np.float64)
+    x, info, ik = _solve(csk, s, d, seed, log=20000, fused=1)
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, d)
+    ref = oracle.mwrk(At, bt, x_star=s.x_star, tol=1e-6, log_len=20000, nthreads=8)
+    assert info["status"] == 0 and ref.status == 0 and info["rse"] <= 1e-6
+    K = _compare_prefix(ik, ref, 1e-9, name=f"FP64 fused launch {m}x{n} d={d}")
+    if K == ref.iters:
+        assert info["iters"] == ref.iters
+    assert np.sum((x - ref.x) ** 2) / np.sum(s.x_star ** 2) <= 1e-12
+    rse, res = oracle.final_check(At, bt, x, s.x_star)
+    assert abs(info["rse"] - rse) <= 1e-12 * rse + 1e-18
+
+
+def test_fused_launch_residual_stop_and_timeout(csk):
+    """fused = 1 without x* (the stopping norm ||bt||^2 assembled from the
+    CTAs' FP64 partials inside the kernel), and the bounded waits of the
+    fused kernel: CTA 0 never publishes -> CSK_ETIMEOUT, the context
+    survives and the next fused solve converges."""
+    s = synth.gaussian_system(2000, 50, 8, np.float64)
+    p = csk.csk_params_default(d=500, seed=8, tol=1e-12, fused=1)
+    x, info = csk.csk_solve(_to(s.A), _to(s.b), p)
+    h, sg = oracle.count_sketch_map(8, 2000, 500)
+    At, bt = oracle.sketch(s.A, s.b, h, sg, 500)
+    ref = oracle.mwrk(At, bt, tol=1e-12)
+    assert info["status"] == 0 and info["resid"] ** 2 <= 1.0001e-12
+    assert abs(info["iters"] - ref.iters) <= 1
+    s2 = synth.gaussian_system(3000, 40, 6, np.float32)
+    x, info, _ = _solve(csk, s2, 400, 6, grid=4, spin_limit=20000, fault_inject=1, fused=1)
+    assert info["status"] == -3
+    x, info, _ = _solve(csk, s2, 400, 6, grid=4, fused=1)
+    assert info["status"] == 0 and info["rse"] <= 1e-6
