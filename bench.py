@@ -115,7 +115,7 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-LOOP_SOURCES = ("iterate.cu", "common.cuh", "reduce.cuh", "async.cuh", "fp64.cuh")
+LOOP_SOURCES = ("iterate.cu", "common.cuh", "reduce.cuh", "async.cuh", "fp64.cuh", "own_sketch.cuh")
 
 
 def _source_hash(*files):
@@ -375,7 +375,7 @@ def run_precision(args):
     return 0
 
 
-def batched_measure(torch, csk, dev, K, warmup, sample=32):
+def batched_measure(torch, csk, dev, K, warmup, sample=32, rank=0, world=1):
     """The batched form: 256 systems (m log-uniform [5000, 200000], n uniform
     [50, 1000], d = 10 n) x 64 right-hand sides, A and X* iid N(0,1) FP32,
     B = A X*.  The launch shape comes from the batched autotuner (installed as
@@ -387,12 +387,19 @@ def batched_measure(torch, csk, dev, K, warmup, sample=32):
     from paper_2004_02480_gb300 import autotune, synth
     S, R = 256, 64
     shapes = synth.batched_shapes(S, 5000, 200000, 50, 1000, seed=7)
-    g = torch.Generator(device=dev).manual_seed(11)
+    # with several replicas each takes its share of the systems (longest
+    # processing time first; every rank computes the same partition)
+    from paper_2004_02480_gb300 import replicas
+    mine = replicas.lpt_partition([replicas.batched_cost(m, n, 10 * n, R) for m, n in shapes],
+                                  world)[rank]
     batch = []
-    for i, (m, n) in enumerate(shapes):
+    for i in mine:
+        m, n = shapes[i]
+        g = torch.Generator(device=dev).manual_seed(11 + 7919 * i)
         A = torch.randn((m, n), generator=g, device=dev, dtype=torch.float32)
         X = torch.randn((n, R), generator=g, device=dev, dtype=torch.float32)
         batch.append(csk.BatchSystem(A=A, B=A @ X, d=10 * n, seed=1000 + i, Xstar=X))
+    S = len(batch)
     ws = torch.empty(csk.csk_solve_batched_workspace_size(batch), dtype=torch.uint8, device=dev)
     tuned = autotune.tune_batched(batch, ws=ws, use_cache=False)
     p = csk.csk_params_default()            # threads = grid = 0: the installed plan
@@ -408,6 +415,9 @@ def batched_measure(torch, csk, dev, K, warmup, sample=32):
     for _ in range(max(1, warmup)):
         graph.replay()
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     e0, e1 = _events(torch, 2)
     e0.record()
     for _ in range(K):
@@ -421,7 +431,7 @@ def batched_measure(torch, csk, dev, K, warmup, sample=32):
     its = np.concatenate([r["iters"] for r in recs])
     # plain single-system GPU CSK on a sample of the same solves (one RHS each)
     rng = np.random.default_rng(3)
-    pairs = [(int(i), int(rng.integers(R))) for i in rng.integers(S, size=sample)]
+    pairs = [(int(i), int(rng.integers(R))) for i in rng.integers(S, size=sample if rank == 0 else 0)]
     per_path = {"gram": [], "gemv": []}
     good = True
     for i, r in pairs:
@@ -441,19 +451,25 @@ def batched_measure(torch, csk, dev, K, warmup, sample=32):
             good &= rr["status"] == 0 and rr["rse"] <= TOL
             per_path[name].append(a0.elapsed_time(a1))
     best_ms = [min(a, b) for a, b in zip(per_path["gram"], per_path["gemv"])]
-    plain = {"solves_per_s": 1e3 / float(np.mean(best_ms)),
-             "gram_solves_per_s": 1e3 / float(np.mean(per_path["gram"])),
-             "gemv_solves_per_s": 1e3 / float(np.mean(per_path["gemv"])),
-             "sampled_solves": len(pairs), "all_converged": bool(good),
-             "how": "csk_solve per (system, RHS), loop CTA count and variant autotuned per shape "
-                    "(autotune.tune_solve) for the GRAM and GEMV paths, faster path per solve"}
-    value = S * R / (ms * 1e-3)
+    plain = None
+    if pairs:
+        plain = {"solves_per_s": 1e3 / float(np.mean(best_ms)),
+                 "gram_solves_per_s": 1e3 / float(np.mean(per_path["gram"])),
+                 "gemv_solves_per_s": 1e3 / float(np.mean(per_path["gemv"])),
+                 "sampled_solves": len(pairs), "all_converged": bool(good),
+                 "how": "csk_solve per (system, RHS), loop CTA count and variant autotuned per "
+                        "shape (autotune.tune_solve) for the GRAM and GEMV paths, faster path "
+                        "per solve"}
+    job = replicas.aggregate(ms * 1e-3, S * R, 0, ok, device=dev)
+    ms = job["elapsed_s"] * 1e3
+    value = job["throughput"]
     return {"solves_per_s": value, "ms_per_launch": ms, "replays": K, "all_converged": bool(ok),
             "iters_mean": float(its.mean()), "iters_max": int(its.max()),
             "tuned": {"threads": tuned["threads"], "grid": tuned["grid"],
                       "candidates_ms": tuned.get("timings")},
             "grid_used": sorted(grids), "plain_single_system": plain,
-            "speedup_over_plain": value / plain["solves_per_s"],
+            "speedup_over_plain": value / plain["solves_per_s"] if plain else None,
+            "replicas": world, "systems_this_rank": S,
             "workload": "256 systems, m log-uniform [5000,200000], n uniform [50,1000], d=10n, "
                         "64 right-hand sides each, FP32, GRAM path, CUDA-graph replay"}
 
@@ -505,19 +521,33 @@ def sketch_gram_measure(torch, csk, dev, reps=5):
 
 
 def run_batched(args):
-    """batched form alone: its own JSON line (solves/s of the graph replay)."""
+    """batched form alone: its own JSON line (solves/s of the graph replay;
+    with N ranks each replays its LPT share of the systems, no collective on
+    the data path, and the job's time is the slowest rank's)."""
     import torch
     from paper_2004_02480_gb300 import csk
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     csk.lib()
-    dev = torch.device("cuda", 0)
-    r = batched_measure(torch, csk, dev, max(1, min(args.steps, 10)), max(1, args.warmup))
+    dev = torch.device("cuda", local)
+    r = batched_measure(torch, csk, dev, max(1, min(args.steps, 10)), max(1, args.warmup),
+                        rank=rank, world=world)
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
     print(json.dumps({
         "metric": "solves/s at RES<=1e-6, batched form (one persistent launch in a CUDA graph)",
-        "value": r["solves_per_s"], "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+        "value": r["solves_per_s"], "unit": "solves/s", "higher_is_better": True, "n_gpus": world,
+        "scaling": "strong",
         "steps": r["replays"], "warmup": max(1, args.warmup), "ms_per_step": r["ms_per_launch"],
         "dtype": "f32", "data": "synthetic (A, X* iid N(0,1), B = A X*)",
         "config": {"workload": r["workload"]}, **{k: v for k, v in r.items() if k != "workload"}}),
         flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
