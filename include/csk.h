@@ -47,6 +47,8 @@ extern "C" {
 typedef enum {
     CSK_OK = 0,            /* converged (in csk_info) / enqueued (return)   */
     CSK_MAXITER = 1,       /* step cap reached before the tolerance         */
+    CSK_INPROGRESS = 2,    /* csk_batched_iterate: the unit's step budget of
+                              this call ran out; call again to continue      */
     CSK_EINVAL = -1,       /* invalid argument (sizes, NULL, workspace)     */
     CSK_ENOMEM = -2,       /* a size overflows the supported index range    */
     CSK_ETIMEOUT = -3,     /* an inter-CTA wait exceeded its poll limit     */
@@ -402,9 +404,45 @@ typedef struct {
     const void *Xstar;    /* nullable, n x nrhs                                 */
     void *Xout;           /* n x nrhs                                           */
     csk_info *info;       /* nrhs records                                       */
+    void *area;           /* nullable: the system's resident area (256-byte
+                             aligned, csk_batched_area_size bytes: its sketch,
+                             Gram matrix and unit states); NULL = carved from
+                             the workspace (csk_solve_batched only)           */
 } csk_system;
 
 size_t csk_solve_batched_workspace_size(const csk_system *sys, int32_t nsys);
+
+/* ----------------------------------------------------------------------
+ * Step-chunked batched solves (continuous batching): the two halves of
+ * csk_solve_batched, for a caller that keeps each system's sketch and Gram
+ * matrix resident and runs its units a chunk of steps at a time, so that
+ * systems arriving later join the next chunk's launch.
+ *
+ * csk_batched_area_size: bytes of one system's resident area.
+ * csk_batched_prepare: Algorithm 1's Initialize for every system (its
+ *   sketch At, Bt, the FP64 row norms and the split-BF16 Gram matrix, as in
+ *   csk_solve_batched) into sys[i].area (required), and resets its units.
+ *   ws: csk_batched_prepare_workspace_size(sys, nsys) bytes of scratch.
+ * csk_batched_iterate: one persistent launch running every unfinished unit
+ *   of the prepared systems for at most step_budget more steps (0 = to the
+ *   end), resuming it where the previous call left it (r, x and the pending
+ *   projection are saved in the area).  A unit that finishes writes Xout and
+ *   its info as csk_solve_batched does; one that does not reports
+ *   CSK_INPROGRESS with iters = steps so far.  Units already finished cost
+ *   nothing.  A unit's arithmetic does not depend on the budget: the same
+ *   steps in the same order, whatever the chunking.  params as for
+ *   csk_solve_batched (the same tol, max_iter, refresh_every on every call
+ *   of a system); ws: csk_batched_iterate_workspace_size(nsys) bytes.
+ * Both return CSK_EINVAL for bad arguments (a NULL area included) and do not
+ * synchronise.
+ * -------------------------------------------------------------------- */
+size_t csk_batched_area_size(int64_t n, int64_t d, int32_t nrhs);
+size_t csk_batched_prepare_workspace_size(const csk_system *sys, int32_t nsys);
+size_t csk_batched_iterate_workspace_size(const csk_system *sys, int32_t nsys);
+int csk_batched_prepare(const csk_system *sys, int32_t nsys, void *ws, size_t ws_bytes,
+                        void *stream);
+int csk_batched_iterate(const csk_system *sys, int32_t nsys, const csk_params *params,
+                        int64_t step_budget, void *ws, size_t ws_bytes, void *stream);
 
 int csk_solve_batched(const csk_system *sys, int32_t nsys, const csk_params *params,
                       void *ws, size_t ws_bytes, void *stream);

@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcsk.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "csk.h")
 
-CSK_OK, CSK_MAXITER = 0, 1
+CSK_OK, CSK_MAXITER, CSK_INPROGRESS = 0, 1, 2
 CSK_EINVAL, CSK_ENOMEM, CSK_ETIMEOUT, CSK_ENUMERIC, CSK_ECUDA, CSK_EUNSUPPORTED = -1, -2, -3, -4, -5, -6
 CSK_F32, CSK_F64 = 0, 1
 GEMV, GRAM, AUTO, UPDATE = 0, 1, 2, 3
@@ -55,7 +55,7 @@ class csk_system(ctypes.Structure):
                 ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
                 ("nrhs", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("d", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("X0", ctypes.c_void_p), ("Xstar", ctypes.c_void_p),
-                ("Xout", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+                ("Xout", ctypes.c_void_p), ("info", ctypes.c_void_p), ("area", ctypes.c_void_p)]
 
 
 INFO_DTYPE = np.dtype([("status", "<i4"), ("path", "<i4"), ("iters", "<i8"), ("rse", "<f8"),
@@ -128,6 +128,16 @@ def lib():
         L.csk_solve_host_many.restype = ctypes.c_int
         L.csk_synth_systems.argtypes = [ctypes.POINTER(csk_synth_system), i32, P]
         L.csk_synth_systems.restype = ctypes.c_int
+        L.csk_batched_area_size.argtypes = [i64, i64, i32]
+        L.csk_batched_area_size.restype = sz
+        for f in ("csk_batched_prepare_workspace_size", "csk_batched_iterate_workspace_size"):
+            getattr(L, f).argtypes = [ctypes.POINTER(csk_system), i32]
+            getattr(L, f).restype = sz
+        L.csk_batched_prepare.argtypes = [ctypes.POINTER(csk_system), i32, P, sz, P]
+        L.csk_batched_prepare.restype = ctypes.c_int
+        L.csk_batched_iterate.argtypes = [ctypes.POINTER(csk_system), i32, ctypes.POINTER(csk_params),
+                                          i64, P, sz, P]
+        L.csk_batched_iterate.restype = ctypes.c_int
         L.csk_solve_batched_set_plan.argtypes = [ctypes.POINTER(csk_system), i32, i32, i32]
         L.csk_solve_batched_set_plan.restype = ctypes.c_int
         L.csk_solve_batched_signature.argtypes = [ctypes.POINTER(csk_system), i32]
@@ -528,6 +538,7 @@ class BatchSystem:
     Xstar: torch.Tensor | None = None   # n x R
     Xout: torch.Tensor | None = None    # n x R (allocated when None)
     info: torch.Tensor | None = None    # R x 64 bytes (allocated when None)
+    area: torch.Tensor | None = None    # resident area (csk_batched_area_size bytes)
 
 
 def _systems(batch: list[BatchSystem]):
@@ -547,7 +558,7 @@ def _systems(batch: list[BatchSystem]):
             y.info = torch.zeros((R, 64), dtype=torch.uint8, device=y.A.device)
         arr[i] = csk_system(_ptr(y.A), m, n, _rowmajor(y.A), _ptr(y.B), y.B.stride(0), R, 0, y.d,
                             y.seed & (2**64 - 1), _ptr(y.X0), _ptr(y.Xstar), _ptr(y.Xout),
-                            _ptr(y.info))
+                            _ptr(y.info), _ptr(y.area))
     return arr
 
 
@@ -602,3 +613,42 @@ def csk_solve_batched_signature(batch: list) -> int:
             m, n, d, R = y
             arr[i] = csk_system(None, m, n, n, None, R, R, 0, d, 0, None, None, None, None)
     return int(lib().csk_solve_batched_signature(arr, len(batch)))
+
+
+def csk_batched_area_size(n: int, d: int, nrhs: int) -> int:
+    """Bytes of one system's resident area (sketch, Gram matrix, unit states)."""
+    return int(lib().csk_batched_area_size(n, d, nrhs))
+
+
+def csk_batched_prepare(batch: list[BatchSystem], *, ws: torch.Tensor | None = None) -> None:
+    """Sketch and Gram matrix of every system into its area (allocated here
+    when the system has none); resets the systems' units.  Enqueued on the
+    current stream."""
+    for y in batch:
+        if y.area is None:
+            R = y.B.shape[1]
+            y.area = torch.empty(csk_batched_area_size(y.A.shape[1], y.d, R), dtype=torch.uint8,
+                                 device=y.A.device)
+    arr = _systems(batch)
+    dev = batch[0].A.device
+    if ws is None:
+        ws = _workspace(int(lib().csk_batched_prepare_workspace_size(arr, len(batch))), dev)
+    rc = lib().csk_batched_prepare(arr, len(batch), _ptr(ws), ws.numel(), _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_batched_prepare")
+
+
+def csk_batched_iterate(batch: list[BatchSystem], params: csk_params, step_budget: int, *,
+                        ws: torch.Tensor | None = None) -> None:
+    """Run every unfinished unit of the prepared systems for at most
+    step_budget more steps (0: to the end).  Enqueued on the current stream;
+    finished units have their Xout column and info written, the others report
+    CSK_INPROGRESS."""
+    arr = _systems(batch)
+    dev = batch[0].A.device
+    if ws is None:
+        ws = _workspace(int(lib().csk_batched_iterate_workspace_size(arr, len(batch))), dev)
+    rc = lib().csk_batched_iterate(arr, len(batch), ctypes.byref(params), int(step_budget),
+                                   _ptr(ws), ws.numel(), _stream(dev))
+    if rc != CSK_OK:
+        raise CskError(rc, "csk_batched_iterate")

@@ -387,6 +387,7 @@ const char* csk_strerror(int status) {
     switch (status) {
         case CSK_OK: return "CSK_OK";
         case CSK_MAXITER: return "CSK_MAXITER: step cap reached";
+        case CSK_INPROGRESS: return "CSK_INPROGRESS: step budget of this call ran out";
         case CSK_EINVAL: return "CSK_EINVAL: invalid argument";
         case CSK_ENOMEM: return "CSK_ENOMEM: size out of supported range";
         case CSK_ETIMEOUT: return "CSK_ETIMEOUT: inter-CTA wait exceeded its poll limit";
@@ -451,7 +452,7 @@ int csk_gram(const float* At, int64_t d, int64_t n, const double* norms2, float*
 }
 
 size_t csk_solve_batched_workspace_size(const csk_system* sys, int32_t nsys) {
-    return batched_workspace_bytes(sys, nsys);
+    return batched_workspace_bytes(sys, nsys, true, true);
 }
 
 int csk_solve_batched(const csk_system* sys, int32_t nsys, const csk_params* params, void* ws,
@@ -479,6 +480,55 @@ int csk_solve_batched(const csk_system* sys, int32_t nsys, const csk_params* par
     int rc = check_stream_device(st);
     if (rc != CSK_OK) return rc;
     return launch_batched(sys, nsys, params, log, ws, ws_bytes, st);
+}
+
+size_t csk_batched_area_size(int64_t n, int64_t d, int32_t nrhs) {
+    if (n < 1 || d < 1 || nrhs < 1 || n > INT_MAX || d > INT_MAX) return 0;
+    return batched_area_bytes(n, d, nrhs);
+}
+
+size_t csk_batched_prepare_workspace_size(const csk_system* sys, int32_t nsys) {
+    return batched_workspace_bytes(sys, nsys, true, false);
+}
+
+size_t csk_batched_iterate_workspace_size(const csk_system* sys, int32_t nsys) {
+    return batched_workspace_bytes(sys, nsys, false, true);
+}
+
+int csk_batched_prepare(const csk_system* sys, int32_t nsys, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!sys || nsys < 1 || !ws) return CSK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    return launch_batched_prepare(sys, nsys, ws, ws_bytes, st);
+}
+
+int csk_batched_iterate(const csk_system* sys, int32_t nsys, const csk_params* params,
+                        int64_t step_budget, void* ws, size_t ws_bytes, void* stream) {
+    if (!sys || nsys < 1 || !params || !ws || step_budget < 0) return CSK_EINVAL;
+    if (!(params->tol >= 0.0) || params->max_iter < 0 || params->refresh_every < 0 ||
+        params->grid < 0 || params->threads < 0)
+        return CSK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CSK_EINVAL;
+    BatchLog log;
+    if (params->ik_log_len > 0 || params->x_log_len > 0) {
+        if (params->log_system < 0 || params->log_system >= nsys || params->log_rhs < 0 ||
+            params->log_rhs >= sys[params->log_system].nrhs ||
+            (params->ik_log_len > 0 && !params->ik_log) || (params->x_log_len > 0 && !params->x_log))
+            return CSK_EINVAL;
+        log.system = params->log_system;
+        log.rhs = params->log_rhs;
+        log.ik = params->ik_log_len > 0 ? params->ik_log : nullptr;
+        log.ik_len = params->ik_log_len;
+        log.x = params->x_log_len > 0 ? static_cast<float*>(params->x_log) : nullptr;
+        log.x_len = params->x_log_len;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = check_stream_device(st);
+    if (rc != CSK_OK) return rc;
+    return launch_batched_iterate(sys, nsys, params, log, step_budget, ws, ws_bytes, st);
 }
 
 int csk_solve_batched_set_plan(const csk_system* sys, int32_t nsys, int32_t threads,
@@ -525,7 +575,7 @@ size_t csk_workspace_size(int64_t m, int64_t n, int64_t d, int32_t nrhs, int32_t
         y.Xout = reinterpret_cast<void*>(any);
         y.info = reinterpret_cast<csk_info*>(any);
         y.m = m; y.n = n; y.lda = n; y.ldb = nrhs; y.nrhs = nrhs; y.d = d;
-        need = std::max(need, batched_workspace_bytes(&y, 1));
+        need = std::max(need, batched_workspace_bytes(&y, 1, true, true));
     }
     return need;
 }

@@ -31,6 +31,18 @@ namespace csk {
 
 namespace {
 
+// State of one (system, right-hand side) unit between calls that run it a
+// step budget at a time (32 bytes, zero = not started).
+struct UnitState {
+    int64_t k;            // steps done
+    int32_t idx;          // the pending projection's row (applied at the next pass), -1 none
+    float alpha;          //   and its step length
+    float threshold;      // tol * ||x*||^2 (or tol * ||bt||^2)
+    int32_t started;      // 1 once the unit has run
+    int32_t done;         // 1 once it has finished (outputs and info written)
+    int32_t pad_;
+};
+
 struct BatchSys {
     const float* At;
     const float* Bt;
@@ -40,6 +52,9 @@ struct BatchSys {
     const float* Xstar;
     float* Xout;
     csk_info* info;
+    UnitState* states;    // nrhs
+    float* rst;           // nrhs x d: residuals of suspended units
+    float* xst;           // nrhs x n: iterates of suspended units
     int64_t ldg;
     int32_t d, n, nrhs, unit_begin;
 };
@@ -100,8 +115,11 @@ struct UnitLog {
     float* x;     int64_t x_len;
 };
 
+// One unit, resumed from its state when it has run before; with budget > 0
+// it stops after `budget` more steps, saves r, x and the pending projection
+// in its state and reports CSK_INPROGRESS (no outputs yet).
 __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
-                           int64_t max_iter, int refresh, const UnitLog& lg) {
+                           int64_t max_iter, int refresh, const UnitLog& lg, int64_t budget) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
     const int d = S.d, n = S.n, R = S.nrhs;
@@ -111,29 +129,42 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
     float* xs = w2s + dpad;
     float* xss = xs + npad;
     int par = 0;
+    UnitState* ust = S.states + rhs;
+    if (ust->done) return;                    // finished in an earlier call
+    const bool resume = ust->started != 0;
+    float* rsave = S.rst + (int64_t)rhs * d;
+    float* xsave = S.xst + (int64_t)rhs * n;
 
     for (int j = tid; j < d; j += nt) {
-        rs[j] = S.Bt[(int64_t)j * R + rhs];
+        rs[j] = resume ? rsave[j] : S.Bt[(int64_t)j * R + rhs];
         const double N = S.N2[j];
         w2s[j] = N > 0.0 ? (float)(1.0 / N) : (N == 0.0 ? -1.0f : NAN);
     }
     for (int c = tid; c < n; c += nt) {
-        xs[c] = S.X0 ? S.X0[(int64_t)c * R + rhs] : 0.0f;
+        xs[c] = resume ? xsave[c] : (S.X0 ? S.X0[(int64_t)c * R + rhs] : 0.0f);
         xss[c] = S.Xstar ? S.Xstar[(int64_t)c * R + rhs] : 0.0f;
     }
     __syncthreads();
     // stopping threshold tol * ||x*||^2 (or tol * ||bt||^2 without x*)
-    double nrm = 0.0;
-    if (S.Xstar) for (int c = tid; c < n; c += nt) nrm += (double)xss[c] * (double)xss[c];
-    else for (int j = tid; j < d; j += nt) nrm += (double)rs[j] * (double)rs[j];
-    nrm = block_sum_f64(nrm, sh);
-    const float threshold = (float)(tol * nrm);
+    float threshold;
+    if (resume) {
+        threshold = ust->threshold;
+    } else {
+        double nrm = 0.0;
+        if (S.Xstar) for (int c = tid; c < n; c += nt) nrm += (double)xss[c] * (double)xss[c];
+        else for (int j = tid; j < d; j += nt) nrm += (double)rs[j] * (double)rs[j];
+        nrm = block_sum_f64(nrm, sh);
+        threshold = (float)(tol * nrm);
+    }
     const bool fresh_r = (S.X0 != nullptr);
     const bool xstar = (S.Xstar != nullptr);
-    int64_t k = 0;
+    int64_t k = resume ? ust->k : 0;
     int status = CSK_OK;
-    int32_t idx = -1;
-    float alpha = 0.0f;
+    int32_t idx = resume ? ust->idx : -1;
+    float alpha = resume ? ust->alpha : 0.0f;
+    const int64_t kend = budget > 0 ? k + budget : INT64_MAX;
+    bool suspended = false;
+    __syncthreads();                          // every thread has read the state
     for (;;) {
         if (k == 0 ? fresh_r : (refresh > 0 && k % refresh == 0)) {
             // r = bt - At x with FP64 accumulation (x0 given, or periodic refresh)
@@ -260,8 +291,32 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
         idx = c.idx;
         alpha = c.alpha;
         ++k;
+        if (k >= kend) { suspended = true; break; }
     }
     __syncthreads();
+    if (suspended) {
+        // r and x as of the last pass; the pending projection (idx, alpha)
+        // is applied by the next call's first pass
+        for (int j = tid; j < d; j += nt) rsave[j] = rs[j];
+        for (int c = tid; c < n; c += nt) xsave[c] = xs[c];
+        if (tid == 0) {
+            ust->k = k;
+            ust->idx = idx;
+            ust->alpha = alpha;
+            ust->threshold = threshold;
+            ust->started = 1;
+            csk_info* info = S.info + rhs;
+            info->status = CSK_INPROGRESS;
+            info->path = CSK_RESID_GRAM;
+            info->iters = k;
+            info->rse = (double)NAN;
+            info->resid = (double)NAN;
+            info->rows = d;
+            info->grid = (int32_t)gridDim.x;
+        }
+        __syncthreads();
+        return;
+    }
     // outputs and final check
     for (int col = tid; col < n; col += nt) S.Xout[(int64_t)col * R + rhs] = xs[col];
     double ee = 0.0, ss = 0.0;
@@ -299,6 +354,8 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
     bb = block_sum_f64(bb, sh);
     empty = block_sum_f64(empty, sh);
     if (tid == 0) {
+        ust->done = 1;
+        ust->k = k;
         csk_info* info = S.info + rhs;
         info->status = status;
         info->path = CSK_RESID_GRAM;
@@ -317,7 +374,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
 
 __global__ void __launch_bounds__(512)
 k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int* counter, float tol,
-                  int64_t max_iter, int refresh, int log_unit, UnitLog lg) {
+                  int64_t max_iter, int refresh, int log_unit, UnitLog lg, int64_t budget) {
     extern __shared__ __align__(16) float sm[];
     __shared__ BatchShared sh;
     for (;;) {
@@ -334,43 +391,71 @@ k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int*
         }
         const BatchSys S = table[lo];
         const UnitLog none = {nullptr, 0, nullptr, 0};
-        solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh, u == log_unit ? lg : none);
+        solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh, u == log_unit ? lg : none,
+                   budget);
     }
 }
 
 inline size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// A system's resident area: its sketch, Gram matrix and unit states, kept on
+// the device between the calls that iterate it (serving keeps it from the
+// request's arrival to its retirement).
+struct AreaLayout {
+    size_t At, Bt, N2, G, states, rst, xst, total;
+};
+
+void area_layout(int64_t n, int64_t d, int32_t nrhs, AreaLayout* A) {
+    size_t o = 0;
+    A->At = o;     o += a256((size_t)d * n * 4);
+    A->Bt = o;     o += a256((size_t)d * nrhs * 4);
+    A->N2 = o;     o += a256((size_t)d * 8);
+    A->G = o;      o += a256((size_t)d * gram_ld((int)d) * 4);
+    A->states = o; o += a256((size_t)nrhs * sizeof(UnitState));
+    A->rst = o;    o += a256((size_t)nrhs * d * 4);
+    A->xst = o;    o += a256((size_t)nrhs * n * 4);
+    A->total = o;
+}
+
+int check_system(const csk_system& y) {
+    if (!y.A || !y.B || !y.Xout || !y.info) return CSK_EINVAL;
+    if (y.m < 1 || y.n < 1 || y.d < 1 || y.lda < y.n || y.nrhs < 1 || y.ldb < y.nrhs)
+        return CSK_EINVAL;
+    if (y.m > INT_MAX || y.n > INT_MAX || y.d > INT_MAX) return CSK_ENOMEM;
+    if (y.area && reinterpret_cast<uintptr_t>(y.area) % 256 != 0) return CSK_EINVAL;
+    return CSK_OK;
+}
+
+// Workspace: sort and Gram-operand scratch (prepare), the descriptor table
+// and unit counter (iterate), and the areas of the systems that bring none.
 struct BatchLayout {
     size_t sort, gscr, table, counter, total;
-    std::vector<size_t> At, Bt, N2, G;
+    std::vector<size_t> area;        // offset in ws of each system's area (if it has none)
     std::vector<int> order;          // systems by decreasing d*n
     int64_t mmax, dmax, nmax;
 };
 
-int batch_layout(const csk_system* sys, int nsys, BatchLayout* L) {
+int batch_layout(const csk_system* sys, int nsys, bool prepare, bool iterate, BatchLayout* L) {
     L->mmax = L->dmax = L->nmax = 0;
     for (int s = 0; s < nsys; ++s) {
-        const csk_system& y = sys[s];
-        if (!y.A || !y.B || !y.Xout || !y.info) return CSK_EINVAL;
-        if (y.m < 1 || y.n < 1 || y.d < 1 || y.lda < y.n || y.nrhs < 1 || y.ldb < y.nrhs)
-            return CSK_EINVAL;
-        if (y.m > INT_MAX || y.n > INT_MAX || y.d > INT_MAX) return CSK_ENOMEM;
-        L->mmax = std::max(L->mmax, y.m);
-        L->dmax = std::max(L->dmax, y.d);
-        L->nmax = std::max(L->nmax, y.n);
+        const int rc = check_system(sys[s]);
+        if (rc != CSK_OK) return rc;
+        L->mmax = std::max(L->mmax, sys[s].m);
+        L->dmax = std::max(L->dmax, sys[s].d);
+        L->nmax = std::max(L->nmax, sys[s].n);
     }
     size_t o = 0;
-    L->sort = o;  o += a256(sort_scratch_bytes(L->mmax, L->dmax));
-    L->gscr = o;  o += a256(gram_scratch_bytes((int)L->dmax, (int)L->nmax));
-    L->table = o; o += a256((size_t)nsys * sizeof(BatchSys));
-    L->counter = o; o += 256;
-    L->At.resize(nsys); L->Bt.resize(nsys); L->N2.resize(nsys); L->G.resize(nsys);
+    L->sort = o;  o += prepare ? a256(sort_scratch_bytes(L->mmax, L->dmax)) : 0;
+    L->gscr = o;  o += prepare ? a256(gram_scratch_bytes((int)L->dmax, (int)L->nmax)) : 0;
+    L->table = o; o += iterate ? a256((size_t)nsys * sizeof(BatchSys)) : 0;
+    L->counter = o; o += iterate ? 256 : 0;
+    L->area.assign(nsys, 0);
     for (int s = 0; s < nsys; ++s) {
-        const csk_system& y = sys[s];
-        L->At[s] = o; o += a256((size_t)y.d * y.n * 4);
-        L->Bt[s] = o; o += a256((size_t)y.d * y.nrhs * 4);
-        L->N2[s] = o; o += a256((size_t)y.d * 8);
-        L->G[s] = o;  o += a256((size_t)y.d * gram_ld((int)y.d) * 4);
+        if (sys[s].area) continue;
+        AreaLayout A;
+        area_layout(sys[s].n, sys[s].d, sys[s].nrhs, &A);
+        L->area[s] = o;
+        o += A.total;
     }
     L->total = o;
     L->order.resize(nsys);
@@ -379,6 +464,10 @@ int batch_layout(const csk_system* sys, int nsys, BatchLayout* L) {
         return sys[a].d * sys[a].n > sys[b].d * sys[b].n;
     });
     return CSK_OK;
+}
+
+char* area_of(const csk_system& y, const BatchLayout& L, int s, char* ws) {
+    return y.area ? static_cast<char*>(y.area) : ws + L.area[s];
 }
 
 }  // namespace
@@ -430,10 +519,16 @@ int set_batched_plan(const csk_system* sys, int nsys, int threads, int grid) {
 
 uint64_t batched_signature(const csk_system* sys, int nsys) { return batch_signature(sys, nsys); }
 
-size_t batched_workspace_bytes(const csk_system* sys, int nsys) {
+size_t batched_workspace_bytes(const csk_system* sys, int nsys, bool prepare, bool iterate) {
     BatchLayout L;
-    if (!sys || nsys < 1 || batch_layout(sys, nsys, &L) != CSK_OK) return 0;
-    return L.total;
+    if (!sys || nsys < 1 || batch_layout(sys, nsys, prepare, iterate, &L) != CSK_OK) return 0;
+    return L.total == 0 ? 256 : L.total;
+}
+
+size_t batched_area_bytes(int64_t n, int64_t d, int32_t nrhs) {
+    AreaLayout A;
+    area_layout(n, d, nrhs, &A);
+    return A.total;
 }
 
 int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int* threads,
@@ -457,38 +552,60 @@ int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int*
     return CSK_OK;
 }
 
-int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
-                   void* ws, size_t ws_bytes, cudaStream_t st) {
-    BatchLayout L;
-    int rc = batch_layout(sys, nsys, &L);
-    if (rc != CSK_OK) return rc;
-    if (ws_bytes < L.total) return CSK_EINVAL;
-    int threads = 0, grid = 0;
-    size_t smem = 0;
-    int t_req = p->threads, g_req = p->grid;
-    if (t_req == 0 && g_req == 0) (void)lookup_plan(sys, nsys, &t_req, &g_req);   // tuned shape
-    rc = plan_batched(L.dmax, L.nmax, t_req, g_req, &threads, &grid, &smem);
-    if (rc != CSK_OK) return rc;
-    char* w = static_cast<char*>(ws);
+// Sketch and Gram matrix of every system into its area, unit states reset.
+int prepare_batched(const csk_system* sys, int nsys, const BatchLayout& L, char* w,
+                    cudaStream_t st) {
     SortScratch s;
     carve_sort_scratch(w + L.sort, L.mmax, L.dmax, &s);
-    std::vector<BatchSys> table(nsys);
-    int units = 0, log_unit = -1;
     for (int q = 0; q < nsys; ++q) {
         const int i = L.order[q];
         const csk_system& y = sys[i];
-        float* At = reinterpret_cast<float*>(w + L.At[i]);
-        float* Bt = reinterpret_cast<float*>(w + L.Bt[i]);
-        double* N2 = reinterpret_cast<double*>(w + L.N2[i]);
-        float* G = reinterpret_cast<float*>(w + L.G[i]);
+        AreaLayout A;
+        area_layout(y.n, y.d, y.nrhs, &A);
+        char* a = area_of(y, L, i, w);
+        float* At = reinterpret_cast<float*>(a + A.At);
+        float* Bt = reinterpret_cast<float*>(a + A.Bt);
+        double* N2 = reinterpret_cast<double*>(a + A.N2);
+        float* G = reinterpret_cast<float*>(a + A.G);
         if (launch_sketch(CSK_F32, y.A, y.lda, y.m, (int)y.n, y.B, y.ldb, y.nrhs, s, (int)y.d,
                           y.seed, At, Bt, N2, st) != cudaSuccess)
             return CSK_ECUDA;
         if (launch_gram_split_bf16(At, (int)y.d, (int)y.n, N2, G, gram_ld((int)y.d), w + L.gscr,
                                    nullptr, st) != cudaSuccess)
             return CSK_ECUDA;
+        if (cudaMemsetAsync(a + A.states, 0, (size_t)y.nrhs * sizeof(UnitState), st) != cudaSuccess)
+            return CSK_ECUDA;
+    }
+    return CSK_OK;
+}
+
+// One persistent launch over every unit of the systems (units already
+// finished return at once), each running at most `budget` steps (0: to the
+// end).
+int iterate_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
+                    int64_t budget, const BatchLayout& L, char* w, cudaStream_t st) {
+    int threads = 0, grid = 0;
+    size_t smem = 0;
+    int t_req = p->threads, g_req = p->grid;
+    if (t_req == 0 && g_req == 0) (void)lookup_plan(sys, nsys, &t_req, &g_req);   // tuned shape
+    int rc = plan_batched(L.dmax, L.nmax, t_req, g_req, &threads, &grid, &smem);
+    if (rc != CSK_OK) return rc;
+    std::vector<BatchSys> table(nsys);
+    int units = 0, log_unit = -1;
+    for (int q = 0; q < nsys; ++q) {
+        const int i = L.order[q];
+        const csk_system& y = sys[i];
+        AreaLayout A;
+        area_layout(y.n, y.d, y.nrhs, &A);
+        char* a = area_of(y, L, i, w);
         BatchSys& e = table[q];
-        e.At = At; e.Bt = Bt; e.N2 = N2; e.G = G;
+        e.At = reinterpret_cast<const float*>(a + A.At);
+        e.Bt = reinterpret_cast<const float*>(a + A.Bt);
+        e.N2 = reinterpret_cast<const double*>(a + A.N2);
+        e.G = reinterpret_cast<const float*>(a + A.G);
+        e.states = reinterpret_cast<UnitState*>(a + A.states);
+        e.rst = reinterpret_cast<float*>(a + A.rst);
+        e.xst = reinterpret_cast<float*>(a + A.xst);
         e.X0 = static_cast<const float*>(y.X0);
         e.Xstar = static_cast<const float*>(y.Xstar);
         e.Xout = static_cast<float*>(y.Xout);
@@ -511,9 +628,45 @@ int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const B
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return CSK_ECUDA;
     const UnitLog lg = {log.ik, log.ik_len, log.x, log.x_len};
     k_iterate_batched<<<grid, threads, smem, st>>>(dtable, nsys, units, counter, (float)p->tol,
-                                                   p->max_iter, p->refresh_every, log_unit, lg);
+                                                   p->max_iter, p->refresh_every, log_unit, lg,
+                                                   budget);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CSK_OK : CSK_ECUDA;
+}
+
+int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
+                   void* ws, size_t ws_bytes, cudaStream_t st) {
+    BatchLayout L;
+    int rc = batch_layout(sys, nsys, true, true, &L);
+    if (rc != CSK_OK) return rc;
+    if (ws_bytes < L.total) return CSK_EINVAL;
+    char* w = static_cast<char*>(ws);
+    rc = prepare_batched(sys, nsys, L, w, st);
+    if (rc != CSK_OK) return rc;
+    return iterate_batched(sys, nsys, p, log, 0, L, w, st);
+}
+
+int launch_batched_prepare(const csk_system* sys, int nsys, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    BatchLayout L;
+    int rc = batch_layout(sys, nsys, true, false, &L);
+    if (rc != CSK_OK) return rc;
+    for (int s = 0; s < nsys; ++s)
+        if (!sys[s].area) return CSK_EINVAL;
+    if (ws_bytes < L.total) return CSK_EINVAL;
+    return prepare_batched(sys, nsys, L, static_cast<char*>(ws), st);
+}
+
+int launch_batched_iterate(const csk_system* sys, int nsys, const csk_params* p,
+                           const BatchLog& log, int64_t budget, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    BatchLayout L;
+    int rc = batch_layout(sys, nsys, false, true, &L);
+    if (rc != CSK_OK) return rc;
+    for (int s = 0; s < nsys; ++s)
+        if (!sys[s].area) return CSK_EINVAL;
+    if (ws_bytes < L.total) return CSK_EINVAL;
+    return iterate_batched(sys, nsys, p, log, budget, L, static_cast<char*>(ws), st);
 }
 
 }  // namespace csk

@@ -141,7 +141,8 @@ cudaError_t launch_final_check(int dtype, const void* At, int64_t ld, int d, int
 size_t final_check_partials(int d);
 
 // -------------------------------------------------------------- batched
-size_t batched_workspace_bytes(const csk_system* sys, int nsys);
+size_t batched_workspace_bytes(const csk_system* sys, int nsys, bool prepare, bool iterate);
+size_t batched_area_bytes(int64_t n, int64_t d, int32_t nrhs);
 // Per-step logs of one (system, right-hand side) pair: the caller's system
 // index and column; ik / x may be NULL.
 struct BatchLog {
@@ -155,6 +156,11 @@ int set_batched_plan(const csk_system* sys, int nsys, int threads, int grid);
 uint64_t batched_signature(const csk_system* sys, int nsys);
 int launch_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
                    void* ws, size_t ws_bytes, cudaStream_t st);
+int launch_batched_prepare(const csk_system* sys, int nsys, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
+int launch_batched_iterate(const csk_system* sys, int nsys, const csk_params* p,
+                           const BatchLog& log, int64_t budget, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
 
 // ----------------------------------------------------------------- Gram
 // G = At At^T (d x d, FP32) from split BF16 operands on the tensor cores;

@@ -65,9 +65,10 @@ def request_bytes(r: Request) -> int:
     ldg = (r.d + 31) // 32 * 32
     core = (up(f * r.m * r.n) + up(f * r.m * r.nrhs) + 2 * up(f * r.n * r.nrhs) + up(64 * r.nrhs))
     sketch = up(f * r.d * r.n) + up(f * r.d * r.nrhs) + up(8 * r.d) + up(f * r.d * ldg)
+    states = up(32 * r.nrhs) + up(f * r.nrhs * r.d) + up(f * r.nrhs * r.n)   # resumable units
     dp, kp = (r.d + 255) // 256 * 256, (r.n + 63) // 64 * 64
     scratch = up(4 * (2 * r.d + 2 * r.m + 2)) + up(4 * dp * kp) + 2048
-    return int(core + sketch + scratch + 4096)
+    return int(core + sketch + states + scratch + 4096)
 
 
 class Arena:

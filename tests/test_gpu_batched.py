@@ -187,3 +187,61 @@ def test_tuned_plan_is_used_and_changes_no_result(csk):
     for y, (X, _, _) in zip(batch, tuned):
         assert torch.equal(y.Xout.cpu(), X)
     csk.csk_solve_batched_set_plan(batch, 0, 0)            # back to the library default
+
+
+def test_step_chunks_give_the_same_bits(csk):
+    """csk_batched_prepare + csk_batched_iterate with a step budget: units
+    report CSK_INPROGRESS between calls, and when every unit has finished,
+    X and IT are bit for bit those of one csk_solve_batched call with the
+    same CTA shape -- the chunking changes no arithmetic."""
+    batch, host = _batch(csk, SHAPES, seed0=60)
+    p = csk.csk_params_default(threads=256, max_iter=20000)
+    ref = [(X.cpu().clone(), [i["iters"] for i in infos], [i["status"] for i in infos])
+           for X, infos in csk.csk_solve_batched(batch, p)]
+    chunked = [csk.BatchSystem(A=y.A, B=y.B, d=y.d, seed=y.seed, Xstar=y.Xstar) for y in batch]
+    csk.csk_batched_prepare(chunked)
+    calls, seen_progress = 0, False
+    while True:
+        csk.csk_batched_iterate(chunked, p, 37)
+        torch.cuda.synchronize()
+        calls += 1
+        st = [np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=csk.INFO_DTYPE)["status"]
+              for y in chunked]
+        if any((s == csk.CSK_INPROGRESS).any() for s in st):
+            seen_progress = True
+            assert calls < 2000
+            continue
+        break
+    assert seen_progress and calls > 1
+    for y, (X, its, sts) in zip(chunked, ref):
+        recs = np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=csk.INFO_DTYPE)
+        assert torch.equal(y.Xout.cpu(), X)
+        assert list(recs["iters"]) == its and list(recs["status"]) == sts
+
+
+def test_systems_join_a_running_batch_between_chunks(csk):
+    """Continuous batching at step-chunk granularity: systems prepared after
+    the first chunks join the next csk_batched_iterate call beside units
+    still running; every unit ends with the bits of its solve alone."""
+    batch, host = _batch(csk, SHAPES, seed0=70)
+    p = csk.csk_params_default(threads=256)
+    first = [csk.BatchSystem(A=y.A, B=y.B, d=y.d, seed=y.seed, Xstar=y.Xstar) for y in batch[:3]]
+    late = [csk.BatchSystem(A=y.A, B=y.B, d=y.d, seed=y.seed, Xstar=y.Xstar) for y in batch[3:]]
+    csk.csk_batched_prepare(first)
+    csk.csk_batched_iterate(first, p, 50)
+    csk.csk_batched_iterate(first, p, 50)
+    csk.csk_batched_prepare(late)
+    active = first + late
+    for _ in range(400):
+        csk.csk_batched_iterate(active, p, 64)
+        torch.cuda.synchronize()
+        if all((np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=csk.INFO_DTYPE)["status"]
+                != csk.CSK_INPROGRESS).all() for y in active):
+            break
+    for y in active:
+        alone = csk.BatchSystem(A=y.A, B=y.B, d=y.d, seed=y.seed, Xstar=y.Xstar)
+        (X1, inf1), = csk.csk_solve_batched([alone], p)
+        recs = np.frombuffer(y.info.cpu().numpy().tobytes(), dtype=csk.INFO_DTYPE)
+        assert torch.equal(y.Xout.cpu(), X1.cpu())
+        assert list(recs["iters"]) == [i["iters"] for i in inf1]
+        assert all(s == 0 for s in recs["status"]) and float(recs["rse"].max()) <= 1e-6
