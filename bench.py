@@ -556,7 +556,7 @@ def run_serving(args):
     [2000, 100000], n [20, 500], d = 8 n, 1-16 right-hand sides), 120 GB budget."""
     from paper_2004_02480_gb300 import serve
     reqs = serve.poisson_requests(args.rate, args.seconds, 0)
-    srv = serve.Server(budget_bytes=120e9)
+    srv = serve.Server(budget_bytes=120e9, chunk=args.chunk, lanes=args.lanes)
     st = srv.run(reqs)
     print(json.dumps({
         "metric": "p50 latency (ms) under Poisson arrivals, continuous batching", "value": st["p50_ms"],
@@ -589,6 +589,8 @@ def main():
                          "Poisson arrivals; noisy: 100000x500 with an inconsistent b")
     ap.add_argument("--seconds", type=float, default=60.0, help="serving: arrival window")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: requests per second")
+    ap.add_argument("--chunk", type=int, default=512, help="serving: steps per unit per tick")
+    ap.add_argument("--lanes", type=int, default=8, help="serving: streams with their own ticks")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

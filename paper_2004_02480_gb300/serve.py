@@ -1,19 +1,18 @@
 """Continuous-batching request loop for CSK solves on one GPU.
 
 Requests (one system A x = B with 1..R right-hand sides each, Algorithm 1 per
-right-hand side) arrive over time.  Whenever one of several CUDA streams has
-no group in flight, the loop admits the arrived requests whose device memory
-fits the HBM budget (up to max_group) and launches them as one group -- their
-data generated in one call, then one csk_solve_batched call -- on that
-stream, so groups overlap on the device and, while every stream is busy,
-arrivals accumulate into larger groups.  Finished groups are retired (results
-copied to the host, memory returned to the arena) as soon as their completion
-event fires.  Latency is measured from a request's arrival to the moment its
-result is on the host.
+right-hand side) arrive over time.  The loop runs on several lanes (CUDA
+streams), each in ticks of `chunk` steps: a tick is one persistent batched
+launch over the units of the lane's admitted requests (csk_batched_iterate,
+resuming each unit where the previous tick left it); requests that arrived
+meanwhile are admitted against the HBM budget and join the next tick of the
+least-loaded lane, their sketch and Gram matrix formed first
+(csk_batched_prepare) and kept resident until they finish.  Latency is
+measured from a request's arrival to the moment its result is on the host.
 
 With a fixed CTA shape (``threads``) a request's arithmetic does not depend
-on the requests it shares a launch with, so its result is the same alone and
-in the mix.
+on the chunking or on the requests it shares a launch with, so its result is
+the same alone and in the mix.
 
 The admission and accounting policy (:class:`Admission`) is plain Python and
 testable without a GPU; :class:`Server` drives the device through the C ABI.
@@ -172,11 +171,44 @@ def poisson_requests(rate: float, seconds: float, seed: int, m_range=(2000, 1000
     return out
 
 
+class Lane:
+    """One stream of the server: its admitted requests and its ticks in flight."""
+
+    def __init__(self, torch, dev, size):
+        self.stream = torch.cuda.Stream(dev)
+        self.mirrors = [torch.empty(size, dtype=torch.uint8).pin_memory() for _ in range(3)]
+        self.active = []          # (request, system, held, info offset)
+        self.ticks = collections.deque()   # (tick id, event, mirror, snapshot)
+        self.deferred = []        # (tick id, request, held, info offset)
+        self.next_tick = 0
+
+    def units(self) -> int:
+        return sum(a[0].nrhs for a in self.active)
+
+
 class Server:
-    """Drives Admission on a GPU: data generation, batched solves, retirement."""
+    """Continuous batching at step-chunk granularity on one GPU.
+
+    The server runs `lanes` independent lanes, each on a CUDA stream of its
+    own.  A lane's tick is one csk_batched_iterate call over the units of the
+    requests it holds, each running at most `chunk` more steps (Algorithm 1
+    resumes where the previous tick left it: the requests' sketches, Gram
+    matrices and unit states stay resident in their arena ranges).  Requests
+    that arrived meanwhile are admitted against the HBM budget, their data
+    generated and their sketch and Gram matrix formed (csk_batched_prepare)
+    on the lane with the fewest units -- preferring a lane with no tick in
+    flight -- and join its next tick.  After each tick the lane's info records
+    are copied to the host in one transfer; a request whose units have all
+    finished is retired, and its memory is returned once the lane's next
+    tick, which still names it with nothing left to do, has completed.  Up to
+    two ticks per lane are in flight, and the lanes overlap on the GPU.  With
+    a fixed CTA shape a request's arithmetic depends neither on the chunking
+    nor on the other requests, so its result is the same alone and in the
+    mix."""
 
     def __init__(self, device="cuda:0", budget_bytes: float = 120e9, threads: int = 256,
-                 max_group: int = 64, streams: int = 8, tol: float = 1e-6, keep_x: bool = False):
+                 chunk: int = 512, lanes: int = 8, max_group: int = 64, tol: float = 1e-6,
+                 keep_x: bool = False, info_bytes: int = 16 << 20, **_):
         import torch
 
         from . import csk
@@ -186,10 +218,15 @@ class Server:
         # the whole budget is reserved once; requests are carved out of it
         self.arena = Arena(int(budget_bytes))
         self.pool = torch.empty(self.arena.size, dtype=torch.uint8, device=self.dev)
-        self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
+        # info records of every admitted request, read back after each tick
+        self.info_arena = Arena(int(info_bytes))
+        self.info_pool = torch.zeros(self.info_arena.size, dtype=torch.uint8, device=self.dev)
+        self.lanes = [Lane(torch, self.dev, self.info_arena.size) for _ in range(max(1, lanes))]
         self.params = csk.csk_params_default(tol=tol, threads=threads)
+        self.chunk = int(chunk)
         self.keep_x = keep_x
-        self.launches = 0
+        self.launches = 0          # admission groups prepared
+        self.ticks = 0
 
     def _take(self, nbytes: int, held: list):
         off = self.arena.alloc(nbytes)
@@ -198,126 +235,162 @@ class Server:
         held.append((off, nbytes))
         return self.pool[off:off + ((nbytes + 3) // 4) * 4]
 
-    def _materialise(self, r: Request, held: list, info, synth: list):
-        """Arena memory for the request's A, B, X* and X; the request's data
-        (a seeded Gaussian system, the stand-in for a request that arrives with
-        its matrix) are generated for the whole group in one call."""
+    def _free(self, r, held, ioff):
+        for off, nb in held:
+            self.arena.release(off, nb)
+        self.info_arena.release(ioff, 64 * r.nrhs)
+        self.adm.release([r])
+
+    def _materialise(self, r: Request, synth: list):
+        """Arena memory for the request's A, B, X*, X and resident area and
+        an info range; None (nothing held) if the arena cannot place it now."""
         f32 = self.torch.float32
-        parts = [r.m * r.n * 4, r.m * r.nrhs * 4, r.n * r.nrhs * 4, r.n * r.nrhs * 4]
+        held = []
+        ioff = self.info_arena.alloc(64 * r.nrhs)
+        if ioff is None:
+            return None
+        area_bytes = self.csk.csk_batched_area_size(r.n, r.d, r.nrhs)
+        parts = [r.m * r.n * 4, r.m * r.nrhs * 4, r.n * r.nrhs * 4, r.n * r.nrhs * 4, area_bytes]
         views = []
         for nb in parts:
             v = self._take(nb, held)
             if v is None:
+                for off, nb2 in held:
+                    self.arena.release(off, nb2)
+                self.info_arena.release(ioff, 64 * r.nrhs)
                 return None
             views.append(v)
         A = views[0].view(f32).view(r.m, r.n)
         B = views[1].view(f32).view(r.m, r.nrhs)
         X = views[2].view(f32).view(r.n, r.nrhs)
         Xo = views[3].view(f32).view(r.n, r.nrhs)
+        info = self.info_pool[ioff:ioff + 64 * r.nrhs].view(r.nrhs, 64)
         synth.append((A, X, B, r.seed))
-        return self.csk.BatchSystem(A=A, B=B, d=r.d, seed=r.seed, Xstar=X, Xout=Xo, info=info)
+        y = self.csk.BatchSystem(A=A, B=B, d=r.d, seed=r.seed, Xstar=X, Xout=Xo, info=info,
+                                 area=views[4][:area_bytes])
+        return y, held, ioff
 
-    def solve_group(self, group: list[Request], stream):
-        """Launch one group on `stream`; None (nothing held) if the arena is
-        too fragmented to place it right now."""
-        torch = self.torch
-        held = []
-        with torch.cuda.stream(stream):
-            systems, synth = [], []
-            # the group's info records sit together: one copy retires it
-            rows = sum(r.nrhs for r in group)
-            infos = self._take(64 * rows, held)
-            o = 0
-            for r in group if infos is not None else ():
-                info = infos[64 * o:64 * (o + r.nrhs)].view(r.nrhs, 64)
-                o += r.nrhs
-                y = self._materialise(r, held, info, synth)
-                if y is None:
-                    break
-                systems.append(y)
-            ws = None
-            if len(systems) == len(group):
-                ws = self._take(max(self.csk.csk_solve_batched_workspace_size(systems), 256), held)
-            if ws is None:
-                for off, nb in held:
-                    self.arena.release(off, nb)
-                return None
-            self.csk.csk_synth_systems(synth)
-            self.csk.csk_solve_batched(systems, self.params, ws=ws, sync=False)
+    def _admit(self, group, lane: Lane):
+        """Data, sketch and Gram matrix of a newly admitted group, enqueued on
+        the lane's stream; the requests that could not be placed go back to
+        the head of the queue."""
+        synth, placed = [], []
+        for i, r in enumerate(group):
+            got = self._materialise(r, synth)
+            if got is None:
+                self.adm.unadmit(group[i:])
+                break
+            placed.append((r,) + got)
+        if placed:
+            with self.torch.cuda.stream(lane.stream):
+                self.csk.csk_synth_systems(synth, device=self.dev)
+                self.csk.csk_batched_prepare([p[1] for p in placed])
             self.launches += 1
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        return systems, held, ev
-
-    def _retire(self, group, systems, held, now):
-        # one device-to-host copy of every info record of the group (the
-        # first range taken by solve_group)
-        off, nb = held[0]
-        recs = np.frombuffer(self.pool[off:off + nb].cpu().numpy().tobytes(),
-                             dtype=self.csk.INFO_DTYPE)
-        o = 0
-        for r, y in zip(group, systems):
-            rr = recs[o:o + r.nrhs]
-            o += r.nrhs
-            r.status = [int(v) for v in rr["status"]]
-            r.rse = [float(v) for v in rr["rse"]]
-            r.iters = [int(v) for v in rr["iters"]]
-            if self.keep_x:
-                r.x = y.Xout.cpu().numpy()
-        for off, nb in held:
-            self.arena.release(off, nb)
-        t = now()
-        for r in group:
-            r.t_done = t
+        return placed
 
     def warm_up(self):
-        """One small untimed group: CUDA context, kernels and libraries warm."""
+        """One small untimed request: CUDA context, kernels and libraries warm."""
         r = Request(-1, 0.0, 4000, 32, 256, 2, 12345)
-        systems, held, ev = self.solve_group([r], self.streams[0])
+        lane = self.lanes[0]
+        self.adm.arrive(r)
+        placed = self._admit(self.adm.admit(), lane)
+        with self.torch.cuda.stream(lane.stream):
+            self.csk.csk_batched_iterate([p[1] for p in placed], self.params, 0)
+        lane.stream.synchronize()
+        for r, y, held, ioff in placed:
+            self._free(r, held, ioff)
+
+    def _tick(self, lane: Lane):
+        torch = self.torch
+        ys = [a[1] for a in lane.active]
+        hi = max(a[3] + 64 * a[0].nrhs for a in lane.active)
+        mi = lane.next_tick % len(lane.mirrors)
+        with torch.cuda.stream(lane.stream):
+            self.csk.csk_batched_iterate(ys, self.params, self.chunk)
+            lane.mirrors[mi][:hi].copy_(self.info_pool[:hi], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(lane.stream)
+        lane.ticks.append((lane.next_tick, ev, mi, list(lane.active)))
+        lane.next_tick += 1
+        self.ticks += 1
+
+    def _collect(self, lane: Lane, now):
+        """Retire the requests the lane's oldest tick finished."""
+        tid, ev, mi, snap = lane.ticks.popleft()
         ev.synchronize()
-        for off, nb in held:
-            self.arena.release(off, nb)
+        keep = []
+        for d_tid, r, held, ioff in lane.deferred:
+            if d_tid <= tid:
+                self._free(r, held, ioff)
+            else:
+                keep.append((d_tid, r, held, ioff))
+        lane.deferred = keep
+        host = lane.mirrors[mi].numpy()
+        done = set()
+        for r, y, held, ioff in snap:
+            if not np.isnan(r.t_done):
+                continue
+            rec = host[ioff:ioff + 64 * r.nrhs]
+            recs = np.frombuffer(rec.tobytes(), dtype=self.csk.INFO_DTYPE)
+            if (recs["status"] != self.csk.CSK_INPROGRESS).all():
+                r.status = [int(v) for v in recs["status"]]
+                r.rse = [float(v) for v in recs["rse"]]
+                r.iters = [int(v) for v in recs["iters"]]
+                if self.keep_x:
+                    r.x = y.Xout.cpu().numpy()
+                r.t_done = now()
+                done.add(r.rid)
+                lane.deferred.append((tid + 1, r, held, ioff))   # the next tick still names it
+        if done:
+            lane.active = [a for a in lane.active if a[0].rid not in done]
 
     def run(self, requests: list[Request]) -> dict:
         self.warm_up()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        # one group in flight per stream: while every stream is busy, arrivals
-        # wait in the admission queue and the next free stream takes them as
-        # one larger group (batches grow with the load)
-        inflight = {}                              # stream index -> group in flight
-        while pending or self.adm.waiting or inflight:
+        lanes = self.lanes
+        while pending or self.adm.waiting or any(l.active or l.ticks for l in lanes):
             t = now()
             while pending and pending[0].arrival <= t:
                 self.adm.arrive(pending.popleft())
-            for si in list(inflight):
-                group, systems, held, ev = inflight[si]
-                if ev.query():
-                    self._retire(group, systems, held, now)
-                    self.adm.release(group)
-                    del inflight[si]
-            free = [si for si in range(len(self.streams)) if si not in inflight]
-            group = self.adm.admit() if free else []
-            launched = None
-            if group:
-                launched = self.solve_group(group, self.streams[free[0]])
-                if launched is None:              # arena fragmented: retry after a retire
-                    if not inflight:
-                        # nothing will be retired: an empty arena could not place the
-                        # group, so waiting would never end
-                        raise RuntimeError(f"group of {len(group)} requests does not fit the "
-                                           "empty arena: request_bytes underestimates it")
-                    self.adm.unadmit(group)
-                    group = []
-            if group:
-                for r in group:
-                    r.t_admit = now()
-                inflight[free[0]] = (group,) + launched
-            elif not inflight and pending:
+            for lane in lanes:
+                if lane.deferred and not lane.ticks:       # no tick in flight names them
+                    for _, r, held, ioff in lane.deferred:
+                        self._free(r, held, ioff)
+                    lane.deferred = []
+            progressed = False
+            if self.adm.waiting:
+                lane = min(lanes, key=lambda l: (len(l.ticks) > 0, l.units()))
+                group = self.adm.admit()
+                if group:
+                    placed = self._admit(group, lane)
+                    for r in group[:len(placed)]:
+                        r.t_admit = now()
+                    lane.active += placed
+                    progressed = bool(placed)
+                    if not placed and not any(l.active or l.ticks for l in lanes):
+                        raise RuntimeError("a request does not fit the empty arena: "
+                                           "request_bytes underestimates it")
+            for lane in lanes:
+                if lane.active and len(lane.ticks) < 2:
+                    self._tick(lane)
+                    progressed = True
+                if lane.ticks and (len(lane.ticks) >= 2 or not lane.active) and \
+                        lane.ticks[0][1].query():
+                    self._collect(lane, now)
+                    progressed = True
+            if progressed:
+                continue
+            if not any(l.active or l.ticks for l in lanes) and pending:
                 time.sleep(max(0.0, min(1e-3, pending[0].arrival - now())))
             else:
-                time.sleep(5e-5)
+                time.sleep(2e-5)
+        for lane in lanes:
+            lane.stream.synchronize()
+            for _, r, held, ioff in lane.deferred:
+                self._free(r, held, ioff)
+            lane.deferred = []
         wall = now()
         lat = np.array([r.t_done - r.arrival for r in requests])
         solves = sum(r.nrhs for r in requests)
@@ -326,9 +399,9 @@ class Server:
                 "solves_per_s": solves / wall, "requests_per_s": len(requests) / wall,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "max_ms": float(lat.max() * 1e3), "groups": self.launches,
-                "peak_bytes": self.adm.peak, "all_converged": bool(ok),
-                "rse_max": max(max(r.rse) for r in requests)}
+                "max_ms": float(lat.max() * 1e3), "groups": self.launches, "ticks": self.ticks,
+                "chunk_steps": self.chunk, "lanes": len(lanes), "peak_bytes": self.adm.peak,
+                "all_converged": bool(ok), "rse_max": max(max(r.rse) for r in requests)}
 
 
 def main():
@@ -339,9 +412,11 @@ def main():
     ap.add_argument("--seconds", type=float, default=60.0)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=512)
+    ap.add_argument("--lanes", type=int, default=8)
     args = ap.parse_args()
     reqs = poisson_requests(args.rate, args.seconds, args.seed)
-    srv = Server(budget_bytes=args.budget_gb * 1e9)
+    srv = Server(budget_bytes=args.budget_gb * 1e9, chunk=args.chunk, lanes=args.lanes)
     print(json.dumps({"workload": f"Poisson {args.rate}/s for {args.seconds} s, m log-uniform "
                       "[2000,100000], n [20,500], d=8n, 1-16 RHS, FP32, A generated on device",
                       **srv.run(reqs)}))
