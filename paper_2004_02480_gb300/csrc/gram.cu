@@ -14,15 +14,20 @@
 // with the FP64 step length.
 //
 // k_gram_tc: persistent, one CTA per SM, 128 x 256 output tiles.
-//   warp 0 / lane 0   TMA producer: 64-wide K chunks of the 128 A-rows and 256
-//                     B-rows into a 4-stage ring (128B swizzle)
+//   warp 0 / lane 0   TMA producer: 32-wide K chunks of hi and lo of the 128
+//                     A-rows and of the 256 B-rows (four boxes, 48 KB) into a
+//                     4-stage ring (64B swizzle)
 //   warp 1 / lane 0   MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32),
-//                     M = 128, N = 256, K = 16, into one of two TMEM
-//                     accumulators (warp 1 allocates all 512 columns)
+//                     M = 128, N = 256, K = 16; per stage the three products
+//                     hi hi^T, hi lo^T, lo hi^T of both K halves (6 MMAs),
+//                     into one of two TMEM accumulators (warp 1 allocates
+//                     all 512 columns)
 //   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
 //                     direct and mirrored global stores, overlapping the
 //                     next tile's MMAs
-// K loop: 3 segments of ceil(n/64) chunks: (hi, hi), (hi, lo), (lo, hi).
+// Loading hi and lo of a chunk once for all three products moves 2/3 of the
+// operand bytes per MMA that three (hi, hi), (hi, lo), (lo, hi) passes over
+// K would, and a 48 KB stage holds 1.5x the MMA work of a (hi, hi) stage.
 // Every mbarrier wait is bounded; on expiry the CTA records CSK_ETIMEOUT,
 // drains its own TMA loads (bounded), frees its TMEM and returns.
 #include <cstdlib>
@@ -38,11 +43,14 @@ namespace csk {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int KPAD = 64;                      // K padded to a multiple of 64 (the error bound's M)
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;          // 16 KB
-constexpr int B_BYTES = BN * BK * 2;          // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int A_BYTES = BM * BK * 2;          // 8 KB per operand (hi or lo)
+constexpr int B_BYTES = BN * BK * 2;          // 16 KB
+// stage: [A hi | A lo | B hi | B lo]
+constexpr int OFF_ALO = A_BYTES, OFF_BHI = 2 * A_BYTES, OFF_BLO = 2 * A_BYTES + B_BYTES;
+constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
 constexpr int TMEM_COLS = 2 * BN;             // two accumulators: MMA and epilogue overlap
 constexpr int kGramThreads = 192;             // 6 warps: TMA, MMA, 4 x epilogue
 constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before giving up
@@ -135,15 +143,15 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05): K-major operand, 128B swizzle,
-// rows of 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 64B swizzle,
+// rows of 64 bytes (BK = 32 BF16), 8-row core groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
     d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;                // stride byte offset
     d |= (uint64_t)1 << 46;                         // descriptor version
-    d |= (uint64_t)2 << 61;                         // swizzle: 128B
+    d |= (uint64_t)4 << 61;                         // swizzle: 64B
     return d;
 }
 
@@ -214,10 +222,10 @@ __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_p
 // Element (r, c) is written, with its mirror (c, r), exactly when c >= r.
 //
 // PAIR: launched in clusters of two CTAs that take the tiles (2p, bj) and
-// (2p + 1, bj) together.  Each loads its own A panel and half of the shared
-// B panel (128 of its 256 rows), multicast into both CTAs' stage, so a stage
-// costs each SM 32 KB of L2 reads instead of 48 KB; each CTA's stage barrier
-// expects all 48 KB, and a stage is refilled only after both CTAs' MMAs
+// (2p + 1, bj) together.  Each loads its own A panels (hi, lo) and half of
+// the shared B panels (128 of their 256 rows), multicast into both CTAs'
+// stage, so a stage costs each SM 32 KB of L2 reads instead of 48 KB; each
+// CTA's stage barrier expects all 48 KB, and a stage is refilled only after both CTAs' MMAs
 // released it (their commits arrive on both CTAs' empty barriers, count 2).
 // Cluster barriers after set-up and before exit keep each CTA resident while
 // its peer may still write into its shared memory.
@@ -261,7 +269,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
     tc_fence_after();
     if (PAIR) cluster_sync_all();          // both CTAs' barriers exist before any load
     const uint32_t tmem = tmem_base_sh;
-    const int nch = 3 * kchunks;
+    const int nch = kchunks;
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
     const int first = PAIR ? (int)blockIdx.x / 2 : (int)blockIdx.x;
     const int step = PAIR ? (int)gridDim.x / 2 : (int)gridDim.x;
@@ -283,19 +291,21 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                         ok = false;
                         break;
                     }
-                    const int seg = c / kchunks, kc = c - seg * kchunks;
-                    const CUtensorMap* ma = seg == 2 ? &map_lo_a : &map_hi_a;
-                    const CUtensorMap* mb = seg == 1 ? &map_lo_b : &map_hi_b;
+                    const int kx = c * BK;
                     const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     mbar_expect_tx(fb, STAGE_BYTES);
-                    tma_load_2d(sa, ma, fb, kc * BK, bi * BM, pol);
-                    if (PAIR)
-                        tma_load_2d_mc(sa + A_BYTES + rank * (B_BYTES / 2),
-                                       seg == 1 ? &map_lo_a : &map_hi_a, fb, kc * BK,
-                                       bj * BN + (int)rank * BM, (uint16_t)3, pol);
-                    else
-                        tma_load_2d(sa + A_BYTES, mb, fb, kc * BK, bj * BN, pol);
+                    tma_load_2d(sa, &map_hi_a, fb, kx, bi * BM, pol);
+                    tma_load_2d(sa + OFF_ALO, &map_lo_a, fb, kx, bi * BM, pol);
+                    if (PAIR) {
+                        const uint32_t half = rank * (B_BYTES / 2);
+                        const int brow = bj * BN + (int)rank * BM;
+                        tma_load_2d_mc(sa + OFF_BHI + half, &map_hi_a, fb, kx, brow, (uint16_t)3, pol);
+                        tma_load_2d_mc(sa + OFF_BLO + half, &map_lo_a, fb, kx, brow, (uint16_t)3, pol);
+                    } else {
+                        tma_load_2d(sa + OFF_BHI, &map_hi_b, fb, kx, bj * BN, pol);
+                        tma_load_2d(sa + OFF_BLO, &map_lo_b, fb, kx, bj * BN, pol);
+                    }
                     issued = g + 1;
                 }
             }
@@ -330,11 +340,16 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                     }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
-                    const uint32_t sb = sa + A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk)
-                        tc_mma_bf16(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
-                                    kIdesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ah = smem_desc_sw64(sa + kk * 32);
+                        const uint64_t al = smem_desc_sw64(sa + OFF_ALO + kk * 32);
+                        const uint64_t bh = smem_desc_sw64(sa + OFF_BHI + kk * 32);
+                        const uint64_t bl = smem_desc_sw64(sa + OFF_BLO + kk * 32);
+                        tc_mma_bf16(dt, ah, bh, kIdesc, (c > 0 || kk > 0) ? 1u : 0u);
+                        tc_mma_bf16(dt, ah, bl, kIdesc, 1u);
+                        tc_mma_bf16(dt, al, bh, kIdesc, 1u);
+                    }
                     if (PAIR) tc_commit_mc(smem_u32(&empty_bar[st]), (uint16_t)3);
                     else tc_commit(smem_u32(&empty_bar[st]));
                 }
@@ -450,7 +465,7 @@ bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_rows) {
     const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -470,13 +485,13 @@ bool gram_pairs_enabled() {
 int64_t gram_ld(int d) { return round_up(d, 32); }
 
 size_t gram_scratch_bytes(int d, int n) {
-    const int64_t dp = round_up(d, BN), kp = round_up(n, BK);
+    const int64_t dp = round_up(d, BN), kp = round_up(n, KPAD);
     return (size_t)(2 * dp * kp * 2 + 1024);
 }
 
 cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* N2, float* G,
                                    int64_t ldg, void* scratch, csk_info* info, cudaStream_t st) {
-    const int dp = (int)round_up(d, BN), kp = (int)round_up(n, BK);
+    const int dp = (int)round_up(d, BN), kp = (int)round_up(n, KPAD);
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(scratch) + 1023) & ~uintptr_t(1023));
     __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base);
     __nv_bfloat16* lo = hi + (size_t)dp * kp;
