@@ -700,6 +700,20 @@ def main():
     m_gbs = (m_it + 1) * gemv_bytes_per_eval(M, N_COLS) / (m_loop * 1e-3) / 1e9
     mwrk = {"ms": m_tot, "loop_ms": m_loop, "iters": m_it, "rse": mrec[0]["rse"],
             "status": mrec[0]["status"], "stream_gbs": m_gbs}
+    # Remark 1's residual-update form on the same A (r -= alpha A A_i^T: one
+    # pass over A per step, against the chosen row), r recomputed every 50 steps
+    pu = csk.csk_params_default(d=0, tol=TOL, path=csk.UPDATE, refresh_every=50)
+    csk.csk_solve(A, b, pu, x_star=xs, ws=wsm)
+    uev = [_events(torch, 5) for _ in range(RM)]
+    urec = []
+    for i in range(RM):
+        csk.set_stage_events(pu, uev[i])
+        _, inf_u = csk.csk_solve(A, b, pu, x_star=xs, ws=wsm)
+        urec.append(inf_u)
+    torch.cuda.synchronize()
+    mwrk["update_ms"] = float(np.median([e[0].elapsed_time(e[4]) for e in uev]))
+    mwrk["update_iters"] = urec[0]["iters"]
+    mwrk["update_rse"] = urec[0]["rse"]
     del wsm
 
     # latency floor of one step: the same CTA count running only the
@@ -795,6 +809,9 @@ def main():
         "comparison": {"mwrk_unsketched_ms": mwrk["ms"], "mwrk_loop_ms": mwrk["loop_ms"],
                        "mwrk_iters": mwrk["iters"], "mwrk_rse": mwrk["rse"],
                        "mwrk_status": mwrk["status"],
+                       "mwrk_update_form_ms": mwrk["update_ms"],
+                       "mwrk_update_form_iters": mwrk["update_iters"],
+                       "mwrk_update_form_rse": mwrk["update_rse"],
                        "mwrk_loop_kernel": "k_iterate_gemv_stream (A streamed from HBM every step)",
                        "mwrk_loop_gbs": mwrk["stream_gbs"],
                        "mwrk_loop_frac_of_" + peak_kind + "_hbm": mwrk["stream_gbs"] / hbm,

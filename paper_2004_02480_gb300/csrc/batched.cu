@@ -154,7 +154,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
         if (S.Xstar) for (int c = tid; c < n; c += nt) nrm += (double)xss[c] * (double)xss[c];
         else for (int j = tid; j < d; j += nt) nrm += (double)rs[j] * (double)rs[j];
         nrm = block_sum_f64(nrm, sh);
-        threshold = (float)(tol * nrm);
+        threshold = stop_threshold<float>(tol, nrm, S.Xstar ? n : d);
     }
     const bool fresh_r = (S.X0 != nullptr);
     const bool xstar = (S.Xstar != nullptr);

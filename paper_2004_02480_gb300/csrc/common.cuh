@@ -69,6 +69,19 @@ struct __align__(32) Slot {
 };
 
 // Status written into csk_info by the first CTA that fails.
+// Threshold of the Section 3 stopping rule (RES <= tol, i.e. stat <= tol *
+// norm) for a statistic that is a sum of `terms` non-negative terms, each a
+// square of a difference, all rounded in type T: tol * norm shrunk by that
+// sum's rounding bound ((terms - 1) u for the additions, 3 u per term, with
+// room for the rounding of the threshold itself), so a computed statistic
+// at or below it proves the exact one is at most tol * norm.
+template <typename T>
+__host__ __device__ __forceinline__ T stop_threshold(double tol, double norm, int64_t terms) {
+    const double u = sizeof(T) == 4 ? 5.9604644775390625e-8 : 1.1102230246251565e-16;   // 2^-24, 2^-53
+    const double f = 1.0 - (double)(terms + 8) * u;      // >= 0: the bound needs (terms + 8) u < 1
+    return (T)(tol * norm * (f > 0.0 ? f : 0.0));
+}
+
 __device__ __forceinline__ void set_status_once(csk_info* info, int32_t st) {
     atomicCAS(reinterpret_cast<int*>(&info->status), 0, st);
 }

@@ -22,15 +22,21 @@
 //                     hi hi^T, hi lo^T, lo hi^T of both K halves (6 MMAs),
 //                     into one of two TMEM accumulators (warp 1 allocates
 //                     all 512 columns)
-//   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
-//                     direct and mirrored global stores, overlapping the
-//                     next tile's MMAs
+//   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns per warp;
+//                     above the diagonal band each 32 x 32 block inside G
+//                     and its transpose are staged in shared memory (128B
+//                     swizzle) and written by TMA tensor stores (one lane
+//                     issues them), otherwise direct and mirrored per-lane
+//                     stores (a tensor store clips at 16-byte granules, so
+//                     a block crossing column d would write past it);
+//                     the epilogue overlaps the next tile's MMAs
 // Loading hi and lo of a chunk once for all three products moves 2/3 of the
 // operand bytes per MMA that three (hi, hi), (hi, lo), (lo, hi) passes over
 // K would, and a 48 KB stage holds 1.5x the MMA work of a (hi, hi) stage.
 // Every mbarrier wait is bounded; on expiry the CTA records CSK_ETIMEOUT,
 // drains its own TMA loads (bounded), frees its TMEM and returns.
 #include <cstdlib>
+#include <cstring>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -51,6 +57,10 @@ constexpr int B_BYTES = BN * BK * 2;          // 16 KB
 // stage: [A hi | A lo | B hi | B lo]
 constexpr int OFF_ALO = A_BYTES, OFF_BHI = 2 * A_BYTES, OFF_BLO = 2 * A_BYTES + B_BYTES;
 constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
+// epilogue staging: per epilogue warp a 32 x 32 FP32 block and its transpose
+constexpr int EPI_BLOCK = 32 * 32 * 4;                      // 4 KB
+constexpr int EPI_BYTES = 4 * 2 * EPI_BLOCK;                // 32 KB
+constexpr size_t kGramSmem = (size_t)STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr int TMEM_COLS = 2 * BN;             // two accumulators: MMA and epilogue overlap
 constexpr int kGramThreads = 192;             // 6 warps: TMA, MMA, 4 x epilogue
 constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before giving up
@@ -89,6 +99,37 @@ __device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* 
         ".multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5, %6;" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "h"(mask), "l"(policy)
         : "memory");
+}
+// L2 policy for G: written once here, read much later -- evict first, so
+// the operands stay resident.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// Shared -> global tensor store of one box at (c0, c1), in this thread's
+// bulk group.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint"
+        " [%0, {%2, %3}], [%1], %4;" ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(c0),
+        "r"(c1), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// This thread's bulk groups have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// ... and have completed.
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
@@ -165,40 +206,65 @@ constexpr uint32_t kIdesc = (1u << 4)                 // D format F32
 
 // Tile order: row blocks are taken in groups of kGroupRows; inside a group the
 // tiles run column block by column block, so the CTAs working at the same
-// time share a few A panels and B panels in L2.  Tiles entirely below the
-// diagonal (no element with col >= row) are skipped.
+// time share a few A panels and B panels in L2.  Only tiles with an element
+// on or above the diagonal are enumerated, and CTA b takes the valid tiles
+// b, b + grid, ... of that order, so no CTA holds more than
+// ceil(valid / grid) of them.
+//
+// Pairs of CTAs take the same order with units of two row blocks (2p and
+// 2p + 1, sharing the B panel of column block bj) in groups of
+// kGroupRows / 2; a pair is valid when its upper row block is.
 constexpr int kGroupRows = 8;     // row blocks per group of the tile order (8, 16, 32, 64 measured; 8 best)
 
-__device__ __forceinline__ bool tile_at(int t, int nbi, int nbj, int* bi, int* bj) {
-    const int per_group = kGroupRows * nbj;
-    const int g = t / per_group, rem = t - g * per_group;
-    *bj = rem / kGroupRows;
-    *bi = g * kGroupRows + (rem - *bj * kGroupRows);
-    return *bi < nbi && (*bj * BN + BN - 1) >= (*bi * BM);
-}
+// Position in the valid-unit order: group g, column block bj, and q, the
+// index among the group's valid units of that column (the valid units of a
+// column are the group's first ones, those whose top row is at most the
+// column block's last column).
+struct TileCursor {
+    int g, bj, q;
+    int nu, nbj, R, UH, ngroups;
 
-// Pair order: the two CTAs of a cluster take row blocks 2p and 2p + 1 of the
-// same column block bj (they share its B panel); pairs are grouped like the
-// row blocks above.  A pair is skipped when both tiles lie below the
-// diagonal (the even one has the larger part above it).
-constexpr int kGroupPairs = kGroupRows / 2;
+    __host__ __device__ int count(int gg, int jj) const {
+        const int lo = gg * R;
+        int top = min(lo + R - 1, nu - 1);
+        top = min(top, (jj * BN + BN - 1) / UH);
+        return top >= lo ? top - lo + 1 : 0;
+    }
+    // first column block with a valid unit in group gg (at most nbj - 1:
+    // the last column block reaches the last unit)
+    __host__ __device__ int first_col(int gg) const {
+        const int need = gg * R * UH - BN + 1;
+        return need <= 0 ? 0 : (need + BN - 1) / BN;
+    }
+    // Moves k valid units on; false past the last one.
+    __host__ __device__ bool advance(int k) {
+        q += k;
+        while (g < ngroups) {
+            const int c = count(g, bj);
+            if (q < c) return true;
+            q -= c;
+            if (++bj == nbj) {
+                ++g;
+                bj = g < ngroups ? first_col(g) : 0;
+            }
+        }
+        return false;
+    }
+    __host__ __device__ int unit() const { return g * R + q; }
+};
 
-__device__ __forceinline__ bool pair_at(int t, int npairs, int nbj, int* p, int* bj) {
-    const int per_group = kGroupPairs * nbj;
-    const int g = t / per_group, rem = t - g * per_group;
-    *bj = rem / kGroupPairs;
-    *p = g * kGroupPairs + (rem - *bj * kGroupPairs);
-    return *p < npairs && (*bj * BN + BN - 1) >= (2 * *p * BM);
-}
-
-// Tile t of this CTA's sequence: (bi, bj), or false to skip it.
+// Cursor at valid unit `first` (false if there are fewer units).
 template <bool PAIR>
-__device__ __forceinline__ bool tile_of(int t, int nbi, int nbj, uint32_t rank, int* bi, int* bj) {
-    if (!PAIR) return tile_at(t, nbi, nbj, bi, bj);
-    int p;
-    if (!pair_at(t, nbi / 2, nbj, &p, bj)) return false;
-    *bi = 2 * p + (int)rank;
-    return true;
+__host__ __device__ __forceinline__ bool tile_cursor(int nbi, int nbj, int first, TileCursor* c) {
+    c->nu = PAIR ? nbi / 2 : nbi;
+    c->R = PAIR ? kGroupRows / 2 : kGroupRows;
+    c->UH = PAIR ? 2 * BM : BM;
+    c->nbj = nbj;
+    c->ngroups = (c->nu + c->R - 1) / c->R;
+    c->g = 0;
+    c->bj = 0;
+    c->q = 0;
+    return c->advance(first);
 }
 
 // ----------------------------------------------------------------- kernels
@@ -233,7 +299,8 @@ template <bool PAIR>
 __global__ void __launch_bounds__(kGramThreads, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ CUtensorMap map_lo_a,
           const __grid_constant__ CUtensorMap map_hi_b, const __grid_constant__ CUtensorMap map_lo_b,
-          int d, int kchunks, int ntiles, int nbi, int nbj, float* __restrict__ G, int64_t ldg,
+          const __grid_constant__ CUtensorMap map_g, int g_tma,
+          int d, int kchunks, int nbi, int nbj, float* __restrict__ G, int64_t ldg,
           csk_info* info) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>(
@@ -281,9 +348,10 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             int64_t g = 0;                 // chunk counter over all tiles of this CTA
             int64_t issued = 0;
             bool ok = true;
-            for (int t = first; t < ntiles && ok; t += step) {
-                int bi, bj;
-                if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
+            TileCursor cur;
+            for (bool more = tile_cursor<PAIR>(nbi, nbj, first, &cur); more && ok;
+                 more = cur.advance(step)) {
+                const int bi = PAIR ? 2 * cur.unit() + (int)rank : cur.unit(), bj = cur.bj;
                 for (int c = 0; c < nch; ++c, ++g) {
                     const int st = (int)(g % STAGES);
                     const int64_t r = g / STAGES;
@@ -321,9 +389,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             int64_t g = 0;
             int tc = 0;
             bool ok = true;
-            for (int t = first; t < ntiles && ok; t += step) {
-                int bi, bj;
-                if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
+            TileCursor cur;
+            for (bool more = tile_cursor<PAIR>(nbi, nbj, first, &cur); more && ok;
+                 more = cur.advance(step)) {
                 const int a = tc & 1, u = tc >> 1;
                 ++tc;
                 if (u > 0 && !mbar_wait(smem_u32(&acc_empty[a]), (uint32_t)((u - 1) & 1))) {
@@ -361,10 +429,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
         // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. + 31
         const int quad = warp & 3;
         const bool vec_ok = (ldg % 4 == 0) && (reinterpret_cast<uintptr_t>(G) % 16 == 0);
+        // staging of this warp: [block | transpose], 1024-byte aligned (128B swizzle)
+        const uint32_t stg = smem_u32(dsm + STAGES * STAGE_BYTES) + (uint32_t)(quad * 2 * EPI_BLOCK);
+        const uint32_t stg_t = stg + EPI_BLOCK;
+        const uint64_t gpol = l2_evict_first_policy();
         int tc = 0;
-        for (int t = first; t < ntiles; t += step) {
-            int bi, bj;
-            if (!tile_of<PAIR>(t, nbi, nbj, rank, &bi, &bj)) continue;
+        TileCursor cur;
+        for (bool more = tile_cursor<PAIR>(nbi, nbj, first, &cur); more; more = cur.advance(step)) {
+            const int bi = PAIR ? 2 * cur.unit() + (int)rank : cur.unit(), bj = cur.bj;
             const int a = tc & 1, u = tc >> 1;
             ++tc;
             const bool ok = mbar_wait(smem_u32(&acc_full[a]), (uint32_t)(u & 1));
@@ -373,14 +445,43 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                 break;
             }
             tc_fence_after();
-            const int row = bi * BM + quad * 32 + lane;
+            const int row0 = bi * BM + quad * 32;
+            const int row = row0 + lane;
             const bool upper = (bj * BN) >= (bi * BM + BM);     // every column > every row
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * BN + c0), v);
                 const int col0 = bj * BN + c0;
-                if (upper) {
+                if (upper && g_tma && row0 + 32 <= d && col0 + 32 <= d) {
+                    // the staging buffers are free once the previous stores read them
+                    if (lane == 0) bulk_wait_read_all();
+                    __syncwarp();
+                    // block: row `lane`, 16-byte chunk j at position j ^ (lane % 8)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t dst = stg + (uint32_t)(lane * 128 + ((j ^ (lane & 7)) << 4));
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst),
+                                     "r"(v[4 * j]), "r"(v[4 * j + 1]), "r"(v[4 * j + 2]),
+                                     "r"(v[4 * j + 3])
+                                     : "memory");
+                    }
+                    // transpose: row q (column col0 + q of G), element `lane`
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const uint32_t dst = stg_t + (uint32_t)(q * 128 +
+                                                                (((lane >> 2) ^ (q & 7)) << 4) +
+                                                                ((lane & 3) << 2));
+                        asm volatile("st.shared.b32 [%0], %1;" ::"r"(dst), "r"(v[q]) : "memory");
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&map_g, stg, col0, row0, gpol);      // G[row0.., col0..]
+                        tma_store_2d(&map_g, stg_t, row0, col0, gpol);    // G[col0.., row0..]
+                        bulk_commit();
+                    }
+                } else if (upper) {
                     if (row < d) {
                         float* dst = G + (int64_t)row * ldg + col0;
                         // streaming stores: G is written once here and read much
@@ -418,6 +519,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&acc_empty[a]));
         }
+        // every tensor store of this warp has completed before the CTA exits
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     }
     tc_fence_before();
     __syncthreads();
@@ -469,6 +573,21 @@ bool make_map(CUtensorMap* map, void* base, int rows, int cols, int box_rows) {
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// G (d x d FP32, row stride ldg) as 32 x 32 boxes with 128B swizzle, for the
+// epilogue's tensor stores; false when G's base or row stride is not a
+// multiple of 16 bytes (the per-lane stores are used then).
+bool make_g_map(CUtensorMap* map, float* G, int d, int64_t ldg) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || reinterpret_cast<uintptr_t>(G) % 16 != 0 || (ldg * 4) % 16 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)d};
+    const cuuint64_t strides[1] = {(cuuint64_t)ldg * 4};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, G, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Pairs of CTAs sharing B panels (the default); CSK_GRAM_PAIR=0 in the
 // environment selects the one-CTA kernel (same products, same bits), for
 // comparisons.
@@ -502,14 +621,16 @@ cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* 
     if (!make_map(&mha, hi, dp, kp, BM) || !make_map(&mla, lo, dp, kp, BM) ||
         !make_map(&mhb, hi, dp, kp, BN) || !make_map(&mlb, lo, dp, kp, BN))
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+    CUtensorMap mg;
+    memset(&mg, 0, sizeof(mg));
+    const int g_tma = make_g_map(&mg, G, d, ldg) ? 1 : 0;
+    const size_t smem = kGramSmem;
     const int nbi = dp / BM, nbj = dp / BN;          // nbi is even (dp is a multiple of BN)
     cudaError_t e;
     if (gram_pairs_enabled()) {
         e = ensure_smem_attr((const void*)k_gram_tc<true>, smem);
         if (e != cudaSuccess) return e;
         const int npairs = nbi / 2;
-        const int ntiles = (npairs + kGroupPairs - 1) / kGroupPairs * kGroupPairs * nbj;
         int valid = 0;
         for (int q = 0; q < npairs; ++q) valid += nbj - q;
         const int pairs = valid < di.sms / 2 ? valid : di.sms / 2;
@@ -525,19 +646,17 @@ cudaError_t launch_gram_split_bf16(const float* At, int d, int n, const double* 
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_gram_tc<true>, mha, mla, mhb, mlb, d, kp / BK, ntiles, nbi,
-                               nbj, G, ldg, info);
+        e = cudaLaunchKernelEx(&cfg, k_gram_tc<true>, mha, mla, mhb, mlb, mg, g_tma, d, kp / BK,
+                               nbi, nbj, G, ldg, info);
         if (e != cudaSuccess) return e;
     } else {
         e = ensure_smem_attr((const void*)k_gram_tc<false>, smem);
         if (e != cudaSuccess) return e;
-        // tile slots of the grouped order (some below the diagonal, skipped)
-        const int ntiles = (nbi + kGroupRows - 1) / kGroupRows * kGroupRows * nbj;
         int valid = 0;
         for (int i = 0; i < nbi; ++i) valid += nbj - (i * BM) / BN;
         const int grid = valid < di.sms ? valid : di.sms;
-        k_gram_tc<false><<<grid, kGramThreads, smem, st>>>(mha, mla, mhb, mlb, d, kp / BK, ntiles,
-                                                           nbi, nbj, G, ldg, info);
+        k_gram_tc<false><<<grid, kGramThreads, smem, st>>>(mha, mla, mhb, mlb, mg, g_tma, d,
+                                                           kp / BK, nbi, nbj, G, ldg, info);
     }
     if (N2) k_gram_diag<<<(d + 255) / 256, 256, 0, st>>>(N2, d, G, ldg);
     note_launches(N2 ? 3 : 2);

@@ -335,7 +335,8 @@ __device__ __forceinline__ void gemv_loop(const IterProblem& p, int R, int cache
             As[e] = At[(int64_t)(r0 + q) * p.ld + c];
         }
     __syncthreads();
-    const T threshold = (T)(p.tol * stop_norm);      // RES <= tol  <=>  stat <= tol ||x*||^2
+    // RES <= tol  <=>  stat <= tol ||x*||^2 (sum over the n columns, or the d rows without x*)
+    const T threshold = stop_threshold<T>(p.tol, stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     const int64_t lda = cache_rows ? (int64_t)n : p.ld;
     const T* Abase = cache_rows ? As : At + (int64_t)r0 * p.ld;
@@ -489,7 +490,7 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
         xsr[i] = (xstar && c4 < n4) ? reinterpret_cast<const float4*>(xstar)[c4]
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float threshold = (float)(p.tol * stop_norm);
+    const float threshold = stop_threshold<float>(p.tol, stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     uint32_t round = round0;
     int64_t k = 0;
@@ -889,7 +890,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
         if (x0 && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(x0)[c], xr[i]);
         if (xstar && c < nv) Chunk<T>::get(reinterpret_cast<const vec*>(xstar)[c], xsr[i]);
     }
-    const T threshold = (T)(p.tol * *p.stop_norm);
+    const T threshold = stop_threshold<T>(p.tol, *p.stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     uint32_t round = 0;
     int64_t k = 0, g = 0;          // g: blocks consumed (the same count in every warp)
@@ -1107,7 +1108,7 @@ k_iterate_gram(IterProblem p, int R) {
     }
     for (int q = tid; q < nr; q += blockDim.x) w2s[q] = weight_of<float>(p.N2[r0 + q]);
     __syncthreads();
-    const float threshold = (float)(p.tol * *p.stop_norm);
+    const float threshold = stop_threshold<float>(p.tol, *p.stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
     const int K = p.refresh_every;
     uint32_t round = 0;

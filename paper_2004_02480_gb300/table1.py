@@ -44,13 +44,15 @@ def run_shape(csk, torch, m: int, n: int, trials: int, dev) -> dict:
     d = n * n
     pc = csk.csk_params_default(d=d, tol=1e-6, max_iter=20000)
     pm = csk.csk_params_default(d=0, tol=1e-6, max_iter=20000)
-    ws = csk._workspace(max(csk.csk_solve_workspace_size(m, n, csk.CSK_F64, pc),
-                            csk.csk_solve_workspace_size(m, n, csk.CSK_F64, pm)), dev)
+    # Remark 1's residual-update form of MWRK (r -= alpha A A_i^T each step)
+    pu = csk.csk_params_default(d=0, tol=1e-6, max_iter=20000, path=csk.UPDATE)
+    ws = csk._workspace(max(csk.csk_solve_workspace_size(m, n, csk.CSK_F64, q)
+                            for q in (pc, pm, pu)), dev)
     x = torch.empty(n, dtype=torch.float64, device=dev)
     info = torch.zeros(64, dtype=torch.uint8, device=dev)
     gen = torch.Generator(device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    it_c, it_m, t_c, t_m, ok = [], [], [], [], True
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    it_c, it_m, it_u, t_c, t_m, t_u, ok = [], [], [], [], [], [], True
     for trial in range(trials):
         gen.manual_seed(1_000_003 * trial + 7919 * m + n)
         A = torch.randn((m, n), generator=gen, dtype=torch.float64, device=dev)
@@ -62,6 +64,7 @@ def run_shape(csk, torch, m: int, n: int, trials: int, dev) -> dict:
             pc.seed = 0
             autotune.tune_solve(A, b, pc, x_star=xs)
             autotune.tune_solve(A, b, pm, x_star=xs)
+            autotune.tune_solve(A, b, pu, x_star=xs)
         pc.seed = trial
         ev[0].record()
         csk.csk_solve(A, b, pc, x_star=xs, x_out=x, info=info, ws=ws, sync=False)
@@ -75,14 +78,22 @@ def run_shape(csk, torch, m: int, n: int, trials: int, dev) -> dict:
         rm = csk.read_info(info)
         it_m.append(rm["iters"])
         ok &= rm["status"] == 0 and rm["rse"] <= 1e-6
+        ev[4].record()
+        csk.csk_solve(A, b, pu, x_star=xs, x_out=x, info=info, ws=ws, sync=False)
+        ev[5].record()
+        ru = csk.read_info(info)
+        it_u.append(ru["iters"])
+        ok &= ru["status"] == 0 and ru["rse"] <= 1e-6
         torch.cuda.synchronize(dev)
         t_c.append(ev[0].elapsed_time(ev[1]))
         t_m.append(ev[2].elapsed_time(ev[3]))
+        t_u.append(ev[4].elapsed_time(ev[5]))
         del A, b, xs
     mean = lambda v: sum(v) / len(v)  # noqa: E731
     out = {"m": m, "n": n, "d": d, "trials": trials, "all_converged": bool(ok),
            "csk_it": mean(it_c), "mwrk_it": mean(it_m), "csk_ms": mean(t_c), "mwrk_ms": mean(t_m),
-           "speedup": mean(t_m) / mean(t_c)}
+           "speedup": mean(t_m) / mean(t_c), "mwrk_update_it": mean(it_u),
+           "mwrk_update_ms": mean(t_u)}
     if (m, n) in PAPER:
         pit, pmit, pcs, pms, psp = PAPER[(m, n)]
         out["paper"] = {"csk_it": pit, "mwrk_it": pmit, "csk_s": pcs, "mwrk_s": pms, "speedup": psp}
@@ -106,13 +117,15 @@ def main(argv=None) -> int:
             r = run_shape(csk, torch, m, n, args.trials, dev)
             rows.append(r)
             print(json.dumps(r), flush=True)
-    print("\n| m | n | d | CSK IT (paper) | MWRK IT (paper) | CSK ms | MWRK ms | speedup (paper) |")
-    print("|---|---|---|---|---|---|---|---|")
+    print("\n| m | n | d | CSK IT (paper) | MWRK IT (paper) | CSK ms | MWRK ms | speedup (paper) "
+          "| MWRK update form: IT, ms |")
+    print("|---|---|---|---|---|---|---|---|---|")
     for r in rows:
         p = r.get("paper", {})
         print(f"| {r['m']} | {r['n']} | {r['d']} | {r['csk_it']:.2f} ({p.get('csk_it', '-')}) | "
               f"{r['mwrk_it']:.2f} ({p.get('mwrk_it', '-')}) | {r['csk_ms']:.3f} | {r['mwrk_ms']:.3f} | "
-              f"{r['speedup']:.2f} ({p.get('speedup', '-')}) |")
+              f"{r['speedup']:.2f} ({p.get('speedup', '-')}) | {r['mwrk_update_it']:.2f}, "
+              f"{r['mwrk_update_ms']:.3f} |")
     return 0 if all(r["all_converged"] for r in rows) else 1
 
 

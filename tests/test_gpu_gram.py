@@ -225,3 +225,35 @@ def test_gram_pair_kernel_equals_single_cta_kernel(csk, tmp_path):
     for k in files["1"].files:
         a, b = files["1"][k], files["0"][k]
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), k
+
+
+@pytest.mark.parametrize("d,n", [(777, 100), (2000, 300), (300, 1000), (5002, 130), (4998, 64)])
+def test_gram_tensor_store_epilogue_equals_lane_stores(csk, d, n):
+    """Tiles above the diagonal band leave the tensor cores through shared
+    memory and TMA tensor stores (each 32 x 32 block inside G and its
+    transpose) when G's rows are 16-byte aligned; with a row stride that is
+    not (ldg % 4 != 0) the same tiles are written by per-lane stores.  Both
+    must give the same bits, G exactly symmetric, and nothing written past
+    column d (d = 777 and 5000 +- 2 are not multiples of 4: a tensor store
+    crossing column d would write the rest of its 16-byte granule)."""
+    g = torch.Generator(device=DEV).manual_seed(d * 7 + n)
+    At = torch.randn((d, n), generator=g, device=DEV)
+    ld_odd = d + (1 if (d + 1) % 4 else 2)
+    Ga = csk.csk_gram(At)                        # ldg = round_up(d, 32): tensor stores
+    Gb = csk.csk_gram(At, ldg=ld_odd)            # per-lane stores
+    torch.cuda.synchronize()
+    a, b = Ga.cpu().numpy(), Gb.cpu().numpy()
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert np.array_equal(a, a.T)
+    _check_G(a, At.cpu().numpy(), rows=np.arange(0, d, max(1, d // 40)))
+    # padding columns past d are untouched on both store paths
+    L = csk.lib()
+    ws = csk._workspace(int(L.csk_gram_workspace_size(d, n)), torch.device(DEV))
+    for ld in (ld_odd, (d + 31) // 32 * 32 + 32):
+        pad = torch.full((d, ld), 7.0, device=DEV)
+        rc = L.csk_gram(At.data_ptr(), d, n, None, pad.data_ptr(), ld, None, ws.data_ptr(),
+                        ws.numel(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert rc == 0
+        assert bool((pad[:, d:] == 7.0).all()), ld
+        assert np.array_equal(pad[:, :d].cpu().numpy().view(np.uint32), b.view(np.uint32)), ld
