@@ -23,10 +23,11 @@
 //                     into one of two TMEM accumulators (warp 1 allocates
 //                     all 512 columns)
 //   warps 2-5         epilogue: tcgen05.ld 32 lanes x 32 columns per warp;
-//                     above the diagonal band each 32 x 32 block inside G
-//                     and its transpose are staged in shared memory (128B
-//                     swizzle) and written by TMA tensor stores (one lane
-//                     issues them), otherwise direct and mirrored per-lane
+//                     each 32 x 32 block wholly above the diagonal and
+//                     inside G, and its transpose, are staged in shared
+//                     memory (128B swizzle) and written by TMA tensor stores
+//                     (one lane issues them); blocks on the diagonal or
+//                     crossing column d use direct and mirrored per-lane
 //                     stores (a tensor store clips at 16-byte granules, so
 //                     a block crossing column d would write past it);
 //                     the epilogue overlaps the next tile's MMAs
@@ -453,7 +454,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * BN + c0), v);
                 const int col0 = bj * BN + c0;
-                if (upper && g_tma && row0 + 32 <= d && col0 + 32 <= d) {
+                // 32 x 32 blocks wholly above the diagonal and inside G go
+                // through the tensor stores (also on the diagonal band tiles)
+                if (g_tma && col0 >= row0 + 32 && row0 + 32 <= d && col0 + 32 <= d) {
                     // the staging buffers are free once the previous stores read them
                     if (lane == 0) bulk_wait_read_all();
                     __syncwarp();
@@ -502,9 +505,10 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi_a, const __grid_constant__ 
                     for (int q = 0; q < 32; ++q)
                         if (col0 + q < d && row < d)
                             __stcs(G + (int64_t)(col0 + q) * ldg + row, __uint_as_float(v[q]));
-                } else {
-                    // tile on the diagonal band: (r, c) and (c, r) are summed in
-                    // different orders, so keep c >= r and mirror it
+                } else if (col0 + 32 > row0) {
+                    // block on the diagonal: (r, c) and (c, r) are summed in
+                    // different orders, so keep c >= r and mirror it (blocks
+                    // wholly below the diagonal are their mirrors' images)
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const int col = col0 + q;
