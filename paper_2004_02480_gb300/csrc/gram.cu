@@ -269,16 +269,50 @@ __host__ __device__ __forceinline__ bool tile_cursor(int nbi, int nbj, int first
 }
 
 // ----------------------------------------------------------------- kernels
+// Each thread converts 8 consecutive columns of a row (k_pad is a multiple
+// of 64, so a chunk never crosses a row): two 16-byte loads of At when the
+// row segment is aligned and inside [0, n), one 16-byte store into hi and
+// one into lo.  Padding rows and columns are written as zeros.
 __global__ void k_split_bf16(const float* __restrict__ At, int d, int n, int d_pad, int k_pad,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-    const int64_t total = (int64_t)d_pad * k_pad;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / k_pad), c = (int)(e - (int64_t)r * k_pad);
-        const float a = (r < d && c < n) ? At[(int64_t)r * n + c] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(a);
-        hi[e] = h;
-        lo[e] = __float2bfloat16_rn(a - __bfloat162float(h));   // a - h is exact
+    const int kc = k_pad / 8;                               // chunks per row
+    const int64_t total = (int64_t)d_pad * kc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t sq = stride / kc;
+    const int sr = (int)(stride - sq * kc);
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t r = e / kc;
+    int c = (int)(e - r * kc);
+    const bool vec = (n % 4 == 0) && (reinterpret_cast<uintptr_t>(At) % 16 == 0);
+    for (; e < total; e += stride) {
+        float a[8];
+        const int c0 = c * 8;
+        const float* src = At + r * (int64_t)n + c0;
+        if (r < d && vec && c0 + 8 <= n) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 v = __ldg(reinterpret_cast<const float4*>(src) + 1);
+            a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+            a[4] = v.x; a[5] = v.y; a[6] = v.z; a[7] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = (r < d && c0 + q < n) ? __ldg(src + q) : 0.0f;
+        }
+        uint32_t h2[4], l2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(a[2 * q]);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(a[2 * q + 1]);
+            // a - h is exact in FP32
+            const __nv_bfloat16 e0 = __float2bfloat16_rn(a[2 * q] - __bfloat162float(h0));
+            const __nv_bfloat16 e1 = __float2bfloat16_rn(a[2 * q + 1] - __bfloat162float(h1));
+            h2[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            l2[q] = (uint32_t)__bfloat16_as_ushort(e0) | ((uint32_t)__bfloat16_as_ushort(e1) << 16);
+        }
+        reinterpret_cast<uint4*>(hi)[e] = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+        reinterpret_cast<uint4*>(lo)[e] = make_uint4(l2[0], l2[1], l2[2], l2[3]);
+        r += sq;
+        c += sr;
+        if (c >= kc) { c -= kc; ++r; }
     }
 }
 
