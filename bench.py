@@ -578,8 +578,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, sketch/Gram and exchange-floor blocks (all outside "
-                         "the timed steps)")
+                    help="skip the batched and sketch/Gram blocks (both outside the timed steps)")
     ap.add_argument("--grid", type=int, default=0, help="loop CTA count (0 = autotune)")
     ap.add_argument("--variant", type=int, default=0, help="loop variant 1-3 (0 = autotune)")
     ap.add_argument("--workload", default="plain",
@@ -718,8 +717,9 @@ def main():
 
     # latency floor of one step: the same CTA count running only the
     # exchange (CTA reduction + mailbox round trip), 2000 rounds per launch
+    # (about 25 ms of GPU time, outside the timed steps)
     floor_us = None
-    if not args.no_extras:
+    if tuned["gemv_variant"] != 3:
         fl_ws = csk._workspace(csk.lib().csk_exchange_floor_workspace_size(recs[0]["grid"]), dev)
         fts = []
         for _ in range(6):
