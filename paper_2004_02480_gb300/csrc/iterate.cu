@@ -492,6 +492,12 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
     }
     const float threshold = stop_threshold<float>(p.tol, stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    // float4 column c4 of ||x - x*||^2 is counted by CTA c4 % G only: this
+    // lane's share of the CPL chunks, fixed for the whole solve
+    uint32_t stat_mask = 0;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i)
+        if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) stat_mask |= 1u << i;
     uint32_t round = round0;
     int64_t k = 0;
     int status = CSK_OK;
@@ -534,10 +540,9 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
             if (!xstar) c.stat += r * r;
         }
         if (xstar && warp == 0) {
-            // float4 column c4 is counted by CTA c4 % G only
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
+                if ((stat_mask >> i) & 1u) {
                     const float t[4] = {xr[i].x - xsr[i].x, xr[i].y - xsr[i].y,
                                         xr[i].z - xsr[i].z, xr[i].w - xsr[i].w};
                     c.stat += chunk_sq(t);
@@ -892,6 +897,12 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     }
     const T threshold = stop_threshold<T>(p.tol, *p.stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
+    // chunk c of ||x - x*||^2 is counted by CTA c % G only: this lane's share
+    // of the CPL chunks, fixed for the whole solve
+    uint32_t stat_mask = 0;
+#pragma unroll
+    for (int i = 0; i < CPL; ++i)
+        if (lane + 32 * i < nv && (lane + 32 * i) % (int)gridDim.x == b) stat_mask |= 1u << i;
     uint32_t round = 0;
     int64_t k = 0, g = 0;          // g: blocks consumed (the same count in every warp)
     int cs = 0;                    // stage of block g and its lap parity
@@ -965,7 +976,7 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
         if (xstar && warp == 0) {
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                if (lane + 32 * i < nv && (lane + 32 * i) % (int)gridDim.x == b) {
+                if ((stat_mask >> i) & 1u) {
                     T t[V];
 #pragma unroll
                     for (int e = 0; e < V; ++e) t[e] = xr[i][e] - xsr[i][e];
