@@ -455,6 +455,7 @@ template <int RPW, int CPL, bool FUSED>
 __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double stop_norm,
                                          uint32_t round0) {
     __shared__ RedShared<float> sh;
+    __shared__ float stat_local;
     int par = 0;
     const int b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -492,12 +493,11 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
     }
     const float threshold = stop_threshold<float>(p.tol, stop_norm, p.xstar ? p.n : p.d);
     const int64_t spin = p.spin_limit > 0 ? p.spin_limit : kDefaultSpin;
-    // float4 column c4 of ||x - x*||^2 is counted by CTA c4 % G only: this
-    // lane's share of the CPL chunks, fixed for the whole solve
-    uint32_t stat_mask = 0;
-#pragma unroll
-    for (int i = 0; i < CPL; ++i)
-        if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) stat_mask |= 1u << i;
+    // With x*, the last warp (which polls no mailbox: the grid has at most
+    // 32 (kWarps - 1) CTAs) sums ||x - x*||^2 over all columns from its own
+    // copy of x during the exchange, so every CTA holds the same statistic
+    // and it stays out of the candidates and the exchange
+    const bool local_stat = xstar != nullptr && (int)gridDim.x <= 32 * (kWarps - 1);
     uint32_t round = round0;
     int64_t k = 0;
     int status = CSK_OK;
@@ -539,10 +539,11 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
             }
             if (!xstar) c.stat += r * r;
         }
-        if (xstar && warp == 0) {
+        if (xstar && !local_stat && warp == 0) {
+            // float4 column c4 is counted by CTA c4 % G only
 #pragma unroll
             for (int i = 0; i < CPL; ++i) {
-                if ((stat_mask >> i) & 1u) {
+                if (lane + 32 * i < n4 && (lane + 32 * i) % (int)gridDim.x == b) {
                     const float t[4] = {xr[i].x - xsr[i].x, xr[i].y - xsr[i].y,
                                         xr[i].z - xsr[i].z, xr[i].w - xsr[i].w};
                     c.stat += chunk_sq(t);
@@ -550,12 +551,26 @@ __device__ __forceinline__ void reg_loop(const IterProblem& p, int R, double sto
             }
         }
         c = block_reduce(c, sh, par);    // candidates differ across lanes
+        if (local_stat && warp == kWarps - 1) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                if (lane + 32 * i < n4) {
+                    const float t[4] = {xr[i].x - xsr[i].x, xr[i].y - xsr[i].y,
+                                        xr[i].z - xsr[i].z, xr[i].w - xsr[i].w};
+                    acc += chunk_sq(t);
+                }
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) stat_local = acc;
+        }
         if (!exchange(p.slots, round, c, spin, p.fault_inject, p.info, sh, par)) {
             status = CSK_ETIMEOUT;
             break;
         }
         ++round;
-        const int dec = decide(c.stat, threshold, k, p.max_iter, c.key);
+        // (stat_local was written before the exchange's barriers)
+        const int dec = decide(local_stat ? stat_local : c.stat, threshold, k, p.max_iter, c.key);
         if (dec != INT_MIN) { status = dec; break; }
         if (stat_owner && lane == 0 && p.ik_log && k < p.ik_log_len) p.ik_log[k] = c.idx;
         if (stat_owner && p.x_log && k < p.x_log_len)
