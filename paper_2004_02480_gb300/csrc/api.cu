@@ -362,6 +362,7 @@ int dev_info(DevInfo* out) {
         DevInfo d;
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, dev);
         g_dev[dev] = d;
     });

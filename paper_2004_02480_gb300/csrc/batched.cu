@@ -22,6 +22,7 @@
 #include <utility>
 #include <vector>
 
+#include "async.cuh"
 #include "common.cuh"
 #include "fp64.cuh"
 #include "kernels.h"
@@ -76,8 +77,12 @@ constexpr int kMaxWarps = 32;
 struct BatchShared {
     RedShared<float, kMaxWarps> red;
     double dbuf[kMaxWarps];
+    uint64_t gbar;          // completion of the bulk copy of a G row's head
     int unit;
+    int fail;               // a staging wait ran out: this CTA stops
 };
+
+constexpr uint32_t kStageWait = 1u << 26;   // try_wait polls for a staged row head
 
 __device__ __forceinline__ double block_sum_f64(double v, BatchShared& sh) {
     v = warp_sum(v);
@@ -118,8 +123,16 @@ struct UnitLog {
 // One unit, resumed from its state when it has run before; with budget > 0
 // it stops after `budget` more steps, saves r, x and the pending projection
 // in its state and reports CSK_INPROGRESS (no outputs yet).
+//
+// G[i_k, 0..H) (H = the launch's staging capacity, a multiple of the CTA's
+// threads, or the whole row when it fits) arrives in shared memory by one
+// bulk copy per step, issued by thread 0 and completed on sh.gbar; the rest
+// of the row streams through registers as before, its first chunk loaded
+// while the copy is in flight.  Each thread scores the same rows in the
+// same order either way, so the results do not depend on H.
 __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
-                           int64_t max_iter, int refresh, const UnitLog& lg, int64_t budget) {
+                           int64_t max_iter, int refresh, const UnitLog& lg, int64_t budget,
+                           int H, uint32_t& gphase) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5,
               nw = nt >> 5;
     const int d = S.d, n = S.n, R = S.nrhs;
@@ -128,6 +141,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
     float* w2s = rs + dpad;
     float* xs = w2s + dpad;
     float* xss = xs + npad;
+    float* gs = xss + npad;                   // staged head of G[idx, :] (16-byte aligned)
     int par = 0;
     UnitState* ust = S.states + rhs;
     if (ust->done) return;                    // finished in an earlier call
@@ -205,17 +219,60 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
         uint32_t bc[4] = {0u, 0u, 0u, 0u};
         int32_t bi[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
         float ba[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        // G[idx, :] in chunks of kGChunk values per thread, the next chunk's
-        // loads issued before the current chunk is scored
+        // the head of G[idx, :] by one bulk copy into shared memory
+        const int Hd = grow ? min(d, H) : 0;
+        if (Hd > 0 && tid == 0) {
+            const uint32_t bytes = (uint32_t)((Hd + 3) & ~3) * 4u;
+            mbar_expect_tx(smem_u32(&sh.gbar), bytes);
+            bulk_g2s(smem_u32(gs), grow, bytes, smem_u32(&sh.gbar));
+        }
+        // the rest of G[idx, :] in chunks of kGChunk values per thread, the
+        // next chunk's loads issued before the current chunk is scored (the
+        // first chunk's while the head is in flight)
+        const int CH = kGChunk * nt;
         float gv[kGChunk];
 #pragma unroll
         for (int q = 0; q < kGChunk; ++q) {
-            const int j = q * nt + tid;
+            const int j = Hd + q * nt + tid;
             gv[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
         }
-        for (int base = 0; base < d; base += kGChunk * nt) {
+        if (Hd > 0) {
+            const bool ok = mbar_wait(smem_u32(&sh.gbar), gphase & 1u, kStageWait);
+            ++gphase;
+            if (!ok) sh.fail = 1;             // seen by all after the reduction's barrier
+            // rows [0, Hd): the chunk's r, weights and staged G values are
+            // read before any r is written back
+            for (int base = 0; base < Hd; base += CH) {
+                float rv[kGChunk], wv[kGChunk], gh[kGChunk];
+#pragma unroll
+                for (int q = 0; q < kGChunk; ++q) {
+                    const int j = base + q * nt + tid;
+                    rv[q] = j < Hd ? rs[j] : 0.0f;
+                    wv[q] = j < Hd ? w2s[j] : -1.0f;
+                    gh[q] = j < Hd ? gs[j] : 0.0f;
+                }
+#pragma unroll
+                for (int q = 0; q < kGChunk; ++q) {
+                    const int j = base + q * nt + tid;
+                    if (j < Hd) {
+                        const float r = (j == idx) ? 0.0f : fmaf(-alpha, gh[q], rv[q]);
+                        rv[q] = r;
+                        const float w = wv[q];
+                        const uint32_t code = (w < 0.0f) ? 0u : key_code(r * r * w);
+                        if (code > bc[q & 3]) { bc[q & 3] = code; bi[q & 3] = j; ba[q & 3] = r * w; }
+                        if (!xstar) c.stat += r * r;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kGChunk; ++q) {
+                    const int j = base + q * nt + tid;
+                    if (j < Hd) rs[j] = rv[q];
+                }
+            }
+        }
+        for (int base = Hd; base < d; base += CH) {
             float gn[kGChunk];
-            const int nb = base + kGChunk * nt;
+            const int nb = base + CH;
 #pragma unroll
             for (int q = 0; q < kGChunk; ++q) {
                 const int j = nb + q * nt + tid;
@@ -280,6 +337,7 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
             }
         }
         c = block_reduce(c, sh.red, par);
+        if (sh.fail) { status = CSK_ETIMEOUT; break; }
         if (c.stat <= threshold) { status = CSK_OK; break; }
         if (k >= max_iter) { status = CSK_MAXITER; break; }
         if (c.key != c.key || c.key < 0.0f) { status = CSK_ENUMERIC; break; }
@@ -374,11 +432,18 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
 
 __global__ void __launch_bounds__(512)
 k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int* counter, float tol,
-                  int64_t max_iter, int refresh, int log_unit, UnitLog lg, int64_t budget) {
+                  int64_t max_iter, int refresh, int log_unit, UnitLog lg, int64_t budget, int H) {
     extern __shared__ __align__(16) float sm[];
     __shared__ BatchShared sh;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&sh.gbar), 1);
+        mbar_fence_init();
+        sh.fail = 0;
+    }
+    __syncthreads();
+    uint32_t gphase = 0;                       // bulk copies completed on sh.gbar
     for (;;) {
-        if (threadIdx.x == 0) sh.unit = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) sh.unit = sh.fail ? nunits : atomicAdd(counter, 1);
         __syncthreads();
         const int u = sh.unit;
         __syncthreads();
@@ -392,8 +457,11 @@ k_iterate_batched(const BatchSys* __restrict__ table, int nsys, int nunits, int*
         const BatchSys S = table[lo];
         const UnitLog none = {nullptr, 0, nullptr, 0};
         solve_unit(S, u - S.unit_begin, sm, sh, tol, max_iter, refresh, u == log_unit ? lg : none,
-                   budget);
+                   budget, H, gphase);
     }
+    // a copy whose wait ran out may still be writing this CTA's shared memory
+    if (sh.fail && threadIdx.x == 0)
+        (void)mbar_wait(smem_u32(&sh.gbar), (gphase - 1u) & 1u, kStageWait);
 }
 
 inline size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -532,15 +600,27 @@ size_t batched_area_bytes(int64_t n, int64_t d, int32_t nrhs) {
 }
 
 int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int* threads,
-                 int* grid, size_t* smem) {
+                 int* grid, size_t* smem, int* head) {
     DevInfo di;
     if (dev_info(&di) != 0) return CSK_ECUDA;
-    const size_t need = (size_t)(2 * ((dmax + 3) & ~3) + 2 * ((nmax + 3) & ~3)) * 4;
+    size_t need = (size_t)(2 * ((dmax + 3) & ~3) + 2 * ((nmax + 3) & ~3)) * 4;
     if (need + sizeof(BatchShared) + 1024 > (size_t)di.smem_optin) return CSK_EUNSUPPORTED;
     // 256 threads: measured faster than 512 on the 256 x 64 workload (shared
     // memory caps both at the same CTAs per SM)
     int t = threads_req > 0 ? threads_req : 256;
     if (t < 64 || t > 512 || (t & 31)) return CSK_EINVAL;
+    // staging of the G rows' heads: what shared memory leaves beside two CTAs
+    // per SM (1 KB of each CTA's share is the system's), whole rows when they
+    // fit, else a multiple of the CTA's threads
+    int64_t H = 0;
+    const int64_t share = (int64_t)di.smem_per_sm / 2 - 1024 - (int64_t)sizeof(BatchShared) -
+                          (int64_t)need;
+    if (share >= 4 * ((dmax + 3) & ~3)) H = (dmax + 3) & ~3;
+    else if (share > 0) H = share / 4 / t * t;
+    const int64_t cap = ((int64_t)di.smem_optin - 1024 - (int64_t)sizeof(BatchShared) - (int64_t)need) / 4;
+    if (H > cap) H = cap / t * t;
+    if (H < 0) H = 0;
+    need += (size_t)H * 4;
     if (ensure_smem_attr((const void*)k_iterate_batched, need) != cudaSuccess) return CSK_ECUDA;
     int per_sm = 0;
     if (cached_occupancy((const void*)k_iterate_batched, t, need, &per_sm) != cudaSuccess ||
@@ -549,6 +629,7 @@ int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int*
     *threads = t;
     *grid = grid_req > 0 ? grid_req : per_sm * di.sms;
     *smem = need;
+    *head = (int)H;
     return CSK_OK;
 }
 
@@ -584,11 +665,11 @@ int prepare_batched(const csk_system* sys, int nsys, const BatchLayout& L, char*
 // end).
 int iterate_batched(const csk_system* sys, int nsys, const csk_params* p, const BatchLog& log,
                     int64_t budget, const BatchLayout& L, char* w, cudaStream_t st) {
-    int threads = 0, grid = 0;
+    int threads = 0, grid = 0, head = 0;
     size_t smem = 0;
     int t_req = p->threads, g_req = p->grid;
     if (t_req == 0 && g_req == 0) (void)lookup_plan(sys, nsys, &t_req, &g_req);   // tuned shape
-    int rc = plan_batched(L.dmax, L.nmax, t_req, g_req, &threads, &grid, &smem);
+    int rc = plan_batched(L.dmax, L.nmax, t_req, g_req, &threads, &grid, &smem, &head);
     if (rc != CSK_OK) return rc;
     std::vector<BatchSys> table(nsys);
     int units = 0, log_unit = -1;
@@ -629,7 +710,7 @@ int iterate_batched(const csk_system* sys, int nsys, const csk_params* p, const 
     const UnitLog lg = {log.ik, log.ik_len, log.x, log.x_len};
     k_iterate_batched<<<grid, threads, smem, st>>>(dtable, nsys, units, counter, (float)p->tol,
                                                    p->max_iter, p->refresh_every, log_unit, lg,
-                                                   budget);
+                                                   budget, head);
     note_launches(1);
     return cudaGetLastError() == cudaSuccess ? CSK_OK : CSK_ECUDA;
 }

@@ -13,6 +13,7 @@ namespace csk {
 struct DevInfo {
     int sms = 0;
     int smem_optin = 0;     // max dynamic shared memory per block (bytes)
+    int smem_per_sm = 0;    // shared memory per multiprocessor (bytes)
     int coop = 0;           // cooperative launch supported
 };
 int dev_info(DevInfo* out);
