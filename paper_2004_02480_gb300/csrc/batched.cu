@@ -101,7 +101,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
     t = (a - (s - bb)) + (b - bb);
 }
 
-constexpr int kGChunk = 8;     // G-row values per thread per chunk (two chunks in flight)
+constexpr int kGChunk = 8;     // G-row values per thread per chunk (two groups of four; two chunks in flight)
 constexpr int kXChunk = 4;     // At-row values per thread in flight at once
 constexpr int kRefreshRows = 4;   // rows a warp sums at once in the FP64 refresh
 
@@ -124,12 +124,13 @@ struct UnitLog {
 // it stops after `budget` more steps, saves r, x and the pending projection
 // in its state and reports CSK_INPROGRESS (no outputs yet).
 //
-// G[i_k, 0..H) (H = the launch's staging capacity, a multiple of the CTA's
-// threads, or the whole row when it fits) arrives in shared memory by one
-// bulk copy per step, issued by thread 0 and completed on sh.gbar; the rest
-// of the row streams through registers as before, its first chunk loaded
-// while the copy is in flight.  Each thread scores the same rows in the
-// same order either way, so the results do not depend on H.
+// G[i_k, 0..H) (H = the launch's staging capacity, a multiple of 4 times the
+// CTA's threads, or the whole row when it fits) arrives in shared memory by
+// one bulk copy per step, issued by thread 0 and completed on sh.gbar; the
+// rest of the row streams through registers, its first chunk loaded while
+// the copy is in flight.  Thread tid scores the groups of four rows g = tid
+// (mod threads) in increasing order either way, so the results do not
+// depend on H.
 __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm, BatchShared& sh, float tol,
                            int64_t max_iter, int refresh, const UnitLog& lg, int64_t budget,
                            int H, uint32_t& gphase) {
@@ -212,102 +213,84 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
             const int col = tid + q * nt;
             av[q] = (arow && col < n) ? __ldg(arow + col) : 0.0f;
         }
-        // Rows tid, tid + nt, ... are scored in increasing order into four
-        // interleaved running maxima (a strict > keeps the first of equal
-        // codes), merged below: the same winner as one sequential scan, with
-        // a quarter of the dependent chain.
+        // Rows come in groups of four consecutive ones: thread tid takes the
+        // groups tid, tid + nt, ... in increasing order (one 16-byte shared-
+        // memory access per array per group), and row 4g + e goes to running
+        // maximum e (a strict > keeps the first of equal codes), merged below:
+        // the same winner as one sequential scan.
         uint32_t bc[4] = {0u, 0u, 0u, 0u};
         int32_t bi[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
         float ba[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        // the head of G[idx, :] by one bulk copy into shared memory
-        const int Hd = grow ? min(d, H) : 0;
-        if (Hd > 0 && tid == 0) {
-            const uint32_t bytes = (uint32_t)((Hd + 3) & ~3) * 4u;
-            mbar_expect_tx(smem_u32(&sh.gbar), bytes);
-            bulk_g2s(smem_u32(gs), grow, bytes, smem_u32(&sh.gbar));
-        }
-        // the rest of G[idx, :] in chunks of kGChunk values per thread, the
-        // next chunk's loads issued before the current chunk is scored (the
-        // first chunk's while the head is in flight)
-        const int CH = kGChunk * nt;
-        float gv[kGChunk];
+        const int ng = (d + 3) >> 2;           // row groups (the last may be partial)
+        float4* rs4 = reinterpret_cast<float4*>(rs);
+        const float4* w4s = reinterpret_cast<const float4*>(w2s);
+        // one group: r -= alpha G[idx, rows] (r_idx = 0 exactly), scored
+        auto group = [&](int g, float4 gg, bool upd) {
+            const int j0 = 4 * g;
+            float4 r4 = rs4[g];
+            const float4 w4 = w4s[g];
+            float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+            const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
+            const float gx[4] = {gg.x, gg.y, gg.z, gg.w};
+            const int nv = min(4, d - j0);
 #pragma unroll
-        for (int q = 0; q < kGChunk; ++q) {
-            const int j = Hd + q * nt + tid;
-            gv[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
-        }
-        if (Hd > 0) {
-            const bool ok = mbar_wait(smem_u32(&sh.gbar), gphase & 1u, kStageWait);
-            ++gphase;
-            if (!ok) sh.fail = 1;             // seen by all after the reduction's barrier
-            // rows [0, Hd): the chunk's r, weights and staged G values are
-            // read before any r is written back
-            for (int base = 0; base < Hd; base += CH) {
-                float rv[kGChunk], wv[kGChunk], gh[kGChunk];
-#pragma unroll
-                for (int q = 0; q < kGChunk; ++q) {
-                    const int j = base + q * nt + tid;
-                    rv[q] = j < Hd ? rs[j] : 0.0f;
-                    wv[q] = j < Hd ? w2s[j] : -1.0f;
-                    gh[q] = j < Hd ? gs[j] : 0.0f;
-                }
-#pragma unroll
-                for (int q = 0; q < kGChunk; ++q) {
-                    const int j = base + q * nt + tid;
-                    if (j < Hd) {
-                        const float r = (j == idx) ? 0.0f : fmaf(-alpha, gh[q], rv[q]);
-                        rv[q] = r;
-                        const float w = wv[q];
-                        const uint32_t code = (w < 0.0f) ? 0u : key_code(r * r * w);
-                        if (code > bc[q & 3]) { bc[q & 3] = code; bi[q & 3] = j; ba[q & 3] = r * w; }
-                        if (!xstar) c.stat += r * r;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kGChunk; ++q) {
-                    const int j = base + q * nt + tid;
-                    if (j < Hd) rs[j] = rv[q];
-                }
-            }
-        }
-        for (int base = Hd; base < d; base += CH) {
-            float gn[kGChunk];
-            const int nb = base + CH;
-#pragma unroll
-            for (int q = 0; q < kGChunk; ++q) {
-                const int j = nb + q * nt + tid;
-                gn[q] = (grow && j < d) ? __ldg(grow + j) : 0.0f;
-            }
-            // the chunk's r and weights are read before any r is written back,
-            // so the rows' shared-memory accesses do not serialise
-            float rv[kGChunk], wv[kGChunk];
-#pragma unroll
-            for (int q = 0; q < kGChunk; ++q) {
-                const int j = base + q * nt + tid;
-                rv[q] = j < d ? rs[j] : 0.0f;
-                wv[q] = j < d ? w2s[j] : -1.0f;
-            }
-#pragma unroll
-            for (int q = 0; q < kGChunk; ++q) {
-                const int j = base + q * nt + tid;
-                if (j < d) {
-                    float r = rv[q];
-                    if (grow) r = (j == idx) ? 0.0f : fmaf(-alpha, gv[q], r);
-                    rv[q] = r;
-                    const float w = wv[q];
+            for (int e = 0; e < 4; ++e) {
+                if (e < nv) {
+                    float r = rr[e];
+                    if (upd) r = (j0 + e == idx) ? 0.0f : fmaf(-alpha, gx[e], r);
+                    rr[e] = r;
+                    const float w = ww[e];
                     const uint32_t code = (w < 0.0f) ? 0u : key_code(r * r * w);
-                    if (code > bc[q & 3]) { bc[q & 3] = code; bi[q & 3] = j; ba[q & 3] = r * w; }
+                    if (code > bc[e]) { bc[e] = code; bi[e] = j0 + e; ba[e] = r * w; }
                     if (!xstar) c.stat += r * r;
                 }
             }
-            if (grow)
+            if (upd) {
+                if (nv == 4) rs4[g] = make_float4(rr[0], rr[1], rr[2], rr[3]);
+                else
+                    for (int e = 0; e < nv; ++e) rs[j0 + e] = rr[e];
+            }
+        };
+        // the head of G[idx, :] by one bulk copy into shared memory
+        const int hg = grow ? min(ng, H >> 2) : 0;      // staged groups
+        if (hg > 0 && tid == 0) {
+            const uint32_t bytes = (uint32_t)hg * 16u;
+            mbar_expect_tx(smem_u32(&sh.gbar), bytes);
+            bulk_g2s(smem_u32(gs), grow, bytes, smem_u32(&sh.gbar));
+        }
+        // the rest of G[idx, :] in chunks of kGChunk / 4 groups per thread,
+        // the next chunk's loads issued before the current chunk is scored
+        // (the first chunk's while the head is in flight)
+        constexpr int KG = kGChunk / 4;
+        const float4* grow4 = reinterpret_cast<const float4*>(grow);
+        float4 gv[KG];
 #pragma unroll
-                for (int q = 0; q < kGChunk; ++q) {
-                    const int j = base + q * nt + tid;
-                    if (j < d) rs[j] = rv[q];
-                }
+        for (int q = 0; q < KG; ++q) {
+            const int g = hg + q * nt + tid;
+            gv[q] = (grow && g < ng) ? __ldg(grow4 + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (hg > 0) {
+            const bool ok = mbar_wait(smem_u32(&sh.gbar), gphase & 1u, kStageWait);
+            ++gphase;
+            if (!ok) sh.fail = 1;             // seen by all after the reduction's barrier
+            const float4* gs4 = reinterpret_cast<const float4*>(gs);
+            for (int g = tid; g < hg; g += nt) group(g, gs4[g], true);
+        }
+        for (int base = hg; base < ng; base += KG * nt) {
+            float4 gn[KG];
+            const int nb = base + KG * nt;
 #pragma unroll
-            for (int q = 0; q < kGChunk; ++q) gv[q] = gn[q];
+            for (int q = 0; q < KG; ++q) {
+                const int g = nb + q * nt + tid;
+                gn[q] = (grow && g < ng) ? __ldg(grow4 + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < KG; ++q) {
+                const int g = base + q * nt + tid;
+                if (g < ng) group(g, gv[q], grow != nullptr);
+            }
+#pragma unroll
+            for (int q = 0; q < KG; ++q) gv[q] = gn[q];
         }
 #pragma unroll
         for (int a = 1; a < 4; ++a)
@@ -611,14 +594,15 @@ int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int*
     if (t < 64 || t > 512 || (t & 31)) return CSK_EINVAL;
     // staging of the G rows' heads: what shared memory leaves beside two CTAs
     // per SM (1 KB of each CTA's share is the system's), whole rows when they
-    // fit, else a multiple of the CTA's threads
+    // fit, else a multiple of 4 t values (whole groups of four rows per
+    // thread, so every thread keeps its rows whatever H is)
     int64_t H = 0;
     const int64_t share = (int64_t)di.smem_per_sm / 2 - 1024 - (int64_t)sizeof(BatchShared) -
                           (int64_t)need;
     if (share >= 4 * ((dmax + 3) & ~3)) H = (dmax + 3) & ~3;
-    else if (share > 0) H = share / 4 / t * t;
+    else if (share > 0) H = share / 4 / (4 * t) * (4 * t);
     const int64_t cap = ((int64_t)di.smem_optin - 1024 - (int64_t)sizeof(BatchShared) - (int64_t)need) / 4;
-    if (H > cap) H = cap / t * t;
+    if (H > cap) H = cap / (4 * t) * (4 * t);
     if (H < 0) H = 0;
     need += (size_t)H * 4;
     if (ensure_smem_attr((const void*)k_iterate_batched, need) != cudaSuccess) return CSK_ECUDA;
