@@ -178,10 +178,14 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
     int32_t idx = resume ? ust->idx : -1;
     float alpha = resume ? ust->alpha : 0.0f;
     const int64_t kend = budget > 0 ? k + budget : INT64_MAX;
+    // next step at a multiple of `refresh` (one division per unit, none per step)
+    int64_t next_refresh = refresh > 0 ? (k + refresh - 1) / refresh * refresh : (k == 0 ? 0 : -1);
     bool suspended = false;
     __syncthreads();                          // every thread has read the state
     for (;;) {
-        if (k == 0 ? fresh_r : (refresh > 0 && k % refresh == 0)) {
+        const bool at_refresh = k == next_refresh;
+        if (at_refresh && refresh > 0) next_refresh += refresh;
+        if (k == 0 ? fresh_r : at_refresh) {
             // r = bt - At x with FP64 accumulation (x0 given, or periodic refresh)
             if (idx >= 0) {
                 const float* arow = S.At + (int64_t)idx * n;

@@ -923,12 +923,15 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
     int cs = 0;                    // stage of block g and its lap parity
     uint32_t clap = 0;
     int status = CSK_OK;
+    int64_t next_fresh = 0;        // next recomputation step of the UPD form (0, K, 2K, ...)
     for (;;) {
         Red<T> c;
         c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
         // dot products against x (GEMV form, and the UPD form's recomputation
         // steps) or against the previous chosen row (UPD update steps)
-        const bool use_x = !UPD || k == 0 || (p.refresh_every > 0 && k % p.refresh_every == 0);
+        const bool fresh = k == next_fresh;
+        if (fresh && p.refresh_every > 0) next_fresh += p.refresh_every;
+        const bool use_x = !UPD || fresh;
         for (int blk = 0; blk < nblk && !stalled; ++blk, ++g) {
             const int s = cs;
             const uint32_t lap = clap;
@@ -1139,9 +1142,11 @@ k_iterate_gram(IterProblem p, int R) {
     const int K = p.refresh_every;
     uint32_t round = 0;
     int64_t k = 0;
+    int64_t next_refresh = 0;      // FP64 refresh steps 0, K, 2K, ... (no division per step)
     int status = CSK_OK;
     for (;;) {
-        if (k == 0 || (K > 0 && k % K == 0)) {
+        if (k == next_refresh) {
+            if (K > 0) next_refresh += K;
             // FP64 refresh r = bt - At x: gather the x slices first; the
             // fence orders this CTA's slice stores before its slot words
             for (int c = c0 + tid; c < c1; c += blockDim.x) xg[c] = xsl[c - c0];
