@@ -389,7 +389,8 @@ int csk_solve_host_many(const csk_host_problem *probs, int32_t count, int32_t dt
  * The host array `sys` is read during the call only, and nothing in the call
  * synchronises, so the sequence can be captured in a CUDA graph.
  * ws: csk_solve_batched_workspace_size(sys, nsys) bytes (sketches, Gram
- * matrices and descriptors of every system).
+ * matrices and descriptors of every system, and the scratch of the prepare
+ * lanes described under csk_batched_prepare).
  * -------------------------------------------------------------------- */
 typedef struct {
     const void *A;        /* m x n FP32, leading dimension lda                  */
@@ -422,7 +423,12 @@ size_t csk_solve_batched_workspace_size(const csk_system *sys, int32_t nsys);
  * csk_batched_prepare: Algorithm 1's Initialize for every system (its
  *   sketch At, Bt, the FP64 row norms and the split-BF16 Gram matrix, as in
  *   csk_solve_batched) into sys[i].area (required), and resets its units.
- *   ws: csk_batched_prepare_workspace_size(sys, nsys) bytes of scratch.
+ *   ws: csk_batched_prepare_workspace_size(sys, nsys) bytes of scratch (one
+ *   sort and one Gram scratch per lane: the systems are prepared on up to
+ *   four streams forked from `stream` and joined back to it before the call's
+ *   later work on `stream`; while `stream` is being captured into a CUDA
+ *   graph and no lane streams exist yet, on `stream` alone).  Each system's
+ *   results do not depend on the lane it ran on.
  * csk_batched_iterate: one persistent launch running every unfinished unit
  *   of the prepared systems for at most step_budget more steps (0 = to the
  *   end), resuming it where the previous call left it (r, x and the pending

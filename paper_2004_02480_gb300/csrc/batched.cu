@@ -483,8 +483,15 @@ int check_system(const csk_system& y) {
 
 // Workspace: sort and Gram-operand scratch (prepare), the descriptor table
 // and unit counter (iterate), and the areas of the systems that bring none.
+// The sketches and Gram matrices of a batch are formed on up to kPrepLanes
+// streams forked from the caller's (each lane with its own sort and Gram
+// scratch), so the short launches of small systems overlap.
+constexpr int kPrepLanes = 4;
+
 struct BatchLayout {
     size_t sort, gscr, table, counter, total;
+    int lanes = 1;                   // prepare lanes the scratch is laid out for
+    size_t sort_stride = 0, gscr_stride = 0;
     std::vector<size_t> area;        // offset in ws of each system's area (if it has none)
     std::vector<int> order;          // systems by decreasing d*n
     int64_t mmax, dmax, nmax;
@@ -500,8 +507,11 @@ int batch_layout(const csk_system* sys, int nsys, bool prepare, bool iterate, Ba
         L->nmax = std::max(L->nmax, sys[s].n);
     }
     size_t o = 0;
-    L->sort = o;  o += prepare ? a256(sort_scratch_bytes(L->mmax, L->dmax)) : 0;
-    L->gscr = o;  o += prepare ? a256(gram_scratch_bytes((int)L->dmax, (int)L->nmax)) : 0;
+    L->lanes = prepare ? std::min(kPrepLanes, std::max(nsys, 1)) : 1;
+    L->sort_stride = prepare ? a256(sort_scratch_bytes(L->mmax, L->dmax)) : 0;
+    L->gscr_stride = prepare ? a256(gram_scratch_bytes((int)L->dmax, (int)L->nmax)) : 0;
+    L->sort = o;  o += (size_t)L->lanes * L->sort_stride;
+    L->gscr = o;  o += (size_t)L->lanes * L->gscr_stride;
     L->table = o; o += iterate ? a256((size_t)nsys * sizeof(BatchSys)) : 0;
     L->counter = o; o += iterate ? 256 : 0;
     L->area.assign(nsys, 0);
@@ -621,14 +631,90 @@ int plan_batched(int64_t dmax, int64_t nmax, int threads_req, int grid_req, int*
     return CSK_OK;
 }
 
+// Streams and events of the prepare lanes, one set per call in flight
+// (kept for reuse): a lane waits for `fork` recorded on the caller's stream,
+// and the caller's stream waits for every lane's `join`.
+struct PrepLanes {
+    int dev = -1;
+    cudaStream_t s[kPrepLanes] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kPrepLanes] = {};
+};
+std::mutex g_lanes_mu;
+std::vector<PrepLanes> g_lanes_idle;
+
+void destroy_lanes(PrepLanes& p) {
+    for (int l = 0; l < kPrepLanes; ++l) {
+        if (p.s[l]) cudaStreamDestroy(p.s[l]);
+        if (p.join[l]) cudaEventDestroy(p.join[l]);
+    }
+    if (p.fork) cudaEventDestroy(p.fork);
+}
+
+// A lane set for this device; false when none is idle and the caller's
+// stream is being captured into a CUDA graph (no stream is created then: the
+// batch is prepared on the caller's stream alone).
+bool acquire_lanes(cudaStream_t st, PrepLanes* out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    {
+        std::lock_guard<std::mutex> lk(g_lanes_mu);
+        for (size_t i = 0; i < g_lanes_idle.size(); ++i)
+            if (g_lanes_idle[i].dev == dev) {
+                *out = g_lanes_idle[i];
+                g_lanes_idle.erase(g_lanes_idle.begin() + (std::ptrdiff_t)i);
+                return true;
+            }
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return false;
+    PrepLanes p;
+    p.dev = dev;
+    bool ok = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l < kPrepLanes && ok; ++l)
+        ok = cudaStreamCreateWithFlags(&p.s[l], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p.join[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        destroy_lanes(p);
+        return false;
+    }
+    *out = p;
+    return true;
+}
+
+void release_lanes(const PrepLanes& p) {
+    std::lock_guard<std::mutex> lk(g_lanes_mu);
+    g_lanes_idle.push_back(p);
+}
+
 // Sketch and Gram matrix of every system into its area, unit states reset.
+// Systems go, largest first, to the lane with the least estimated work so
+// far (d^2 n for the Gram matrix plus m n for the sketch); a system's result
+// does not depend on its lane.
 int prepare_batched(const csk_system* sys, int nsys, const BatchLayout& L, char* w,
                     cudaStream_t st) {
-    SortScratch s;
-    carve_sort_scratch(w + L.sort, L.mmax, L.dmax, &s);
-    for (int q = 0; q < nsys; ++q) {
+    PrepLanes pl;
+    const bool forked = L.lanes > 1 && acquire_lanes(st, &pl);
+    const int nl = forked ? L.lanes : 1;
+    SortScratch sc[kPrepLanes];
+    for (int l = 0; l < nl; ++l)
+        carve_sort_scratch(w + L.sort + (size_t)l * L.sort_stride, L.mmax, L.dmax, &sc[l]);
+    int rc = CSK_OK;
+    if (forked) {
+        if (cudaEventRecord(pl.fork, st) != cudaSuccess) rc = CSK_ECUDA;
+        for (int l = 0; l < nl && rc == CSK_OK; ++l)
+            if (cudaStreamWaitEvent(pl.s[l], pl.fork, 0) != cudaSuccess) rc = CSK_ECUDA;
+    }
+    double load[kPrepLanes] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nsys && rc == CSK_OK; ++q) {
         const int i = L.order[q];
         const csk_system& y = sys[i];
+        int lane = 0;
+        for (int l = 1; l < nl; ++l)
+            if (load[l] < load[lane]) lane = l;
+        load[lane] += (double)y.d * (double)y.d * (double)y.n + (double)y.m * (double)y.n;
+        cudaStream_t ls = forked ? pl.s[lane] : st;
         AreaLayout A;
         area_layout(y.n, y.d, y.nrhs, &A);
         char* a = area_of(y, L, i, w);
@@ -636,16 +722,24 @@ int prepare_batched(const csk_system* sys, int nsys, const BatchLayout& L, char*
         float* Bt = reinterpret_cast<float*>(a + A.Bt);
         double* N2 = reinterpret_cast<double*>(a + A.N2);
         float* G = reinterpret_cast<float*>(a + A.G);
-        if (launch_sketch(CSK_F32, y.A, y.lda, y.m, (int)y.n, y.B, y.ldb, y.nrhs, s, (int)y.d,
-                          y.seed, At, Bt, N2, st) != cudaSuccess)
-            return CSK_ECUDA;
-        if (launch_gram_split_bf16(At, (int)y.d, (int)y.n, N2, G, gram_ld((int)y.d), w + L.gscr,
-                                   nullptr, st) != cudaSuccess)
-            return CSK_ECUDA;
-        if (cudaMemsetAsync(a + A.states, 0, (size_t)y.nrhs * sizeof(UnitState), st) != cudaSuccess)
-            return CSK_ECUDA;
+        if (launch_sketch(CSK_F32, y.A, y.lda, y.m, (int)y.n, y.B, y.ldb, y.nrhs, sc[lane], (int)y.d,
+                          y.seed, At, Bt, N2, ls) != cudaSuccess ||
+            launch_gram_split_bf16(At, (int)y.d, (int)y.n, N2, G, gram_ld((int)y.d),
+                                   w + L.gscr + (size_t)lane * L.gscr_stride, nullptr,
+                                   ls) != cudaSuccess ||
+            cudaMemsetAsync(a + A.states, 0, (size_t)y.nrhs * sizeof(UnitState), ls) != cudaSuccess)
+            rc = CSK_ECUDA;
     }
-    return CSK_OK;
+    if (forked) {
+        // join every lane back, also after an error, so no lane work is left
+        // unordered with the caller's stream
+        for (int l = 0; l < nl; ++l)
+            if (cudaEventRecord(pl.join[l], pl.s[l]) != cudaSuccess ||
+                cudaStreamWaitEvent(st, pl.join[l], 0) != cudaSuccess)
+                rc = CSK_ECUDA;
+        release_lanes(pl);
+    }
+    return rc;
 }
 
 // One persistent launch over every unit of the systems (units already
