@@ -273,6 +273,25 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
             const int g = hg + q * nt + tid;
             gv[q] = (grow && g < ng) ? __ldg(grow4 + g) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        // x += alpha At[idx, :] and ||x - x*||^2 (nothing here reads G): done
+        // while the head of the G row is in flight
+        for (int base = 0; base < n; base += kXChunk * nt) {
+#pragma unroll
+            for (int q = 0; q < kXChunk; ++q) {
+                const int col = base + q * nt + tid;
+                if (col < n) {
+                    float x = xs[col];
+                    if (arow) {
+                        x = fmaf(alpha, base == 0 ? av[q] : __ldg(arow + col), x);
+                        xs[col] = x;
+                    }
+                    if (S.Xstar) {
+                        const float t = x - xss[col];
+                        c.stat += t * t;
+                    }
+                }
+            }
+        }
         if (hg > 0) {
             const bool ok = mbar_wait(smem_u32(&sh.gbar), gphase & 1u, kStageWait);
             ++gphase;
@@ -305,23 +324,6 @@ __device__ __forceinline__ void solve_unit(const BatchSys& S, int rhs, float* sm
             c.key = bc[0] == 0xFFFFFFFFu ? NAN : __uint_as_float(bc[0] - 1u);
             c.alpha = ba[0];
             c.idx = bi[0];
-        }
-        for (int base = 0; base < n; base += kXChunk * nt) {
-#pragma unroll
-            for (int q = 0; q < kXChunk; ++q) {
-                const int col = base + q * nt + tid;
-                if (col < n) {
-                    float x = xs[col];
-                    if (arow) {
-                        x = fmaf(alpha, base == 0 ? av[q] : __ldg(arow + col), x);
-                        xs[col] = x;
-                    }
-                    if (S.Xstar) {
-                        const float t = x - xss[col];
-                        c.stat += t * t;
-                    }
-                }
-            }
         }
         c = block_reduce(c, sh.red, par);
         if (sh.fail) { status = CSK_ETIMEOUT; break; }
