@@ -57,14 +57,14 @@ def candidates(sms: int, rows: int | None = None):
     """CTA counts to time: fractions of the SM count, and for problems small
     enough that a few dozen CTAs hold all rows (a cheaper exchange), the
     counts 8..64 that leave at least 4 rows per CTA; also, for each number r
-    = 1..8 of rows a warp of the register loop holds (8 warps a CTA), the
+    = 1..10 of rows a warp of the register loop holds (8 warps a CTA), the
     fewest CTAs that hold every row at r rows per warp (the exchange gets
     cheaper with fewer CTAs, the step's arithmetic dearer)."""
     fr = [1.0, 0.9, 0.84, 0.75, 0.66, 0.6, 0.5]
     out = {max(1, int(round(sms * f))) for f in fr}
     if rows is not None:
         out |= {g for g in (8, 12, 16, 24, 32, 40, 48, 64) if g <= sms and 4 * g <= rows}
-        for r in range(1, 9):
+        for r in range(1, 11):
             g = -(-rows // (8 * r))
             if 1 <= g <= sms and 4 * g <= rows:
                 out.add(g)

@@ -725,14 +725,16 @@ k_fused_reg(IterProblem p, FusedSketch f, int R) {
     reg_loop<RPW, CPL, true>(p, R, stop, round);
 }
 
-// Register-resident variants: (rows per warp, float4 per lane per row).
+// Register-resident variants: (rows per warp, float4 per lane per row); 9 and
+// 10 rows a warp (rows of up to 512 columns) let fewer CTAs hold the sketch.
 #define CSK_REG_VARIANTS(X) \
     X(1, 1) X(2, 1) X(3, 1) X(4, 1) X(6, 1) X(8, 1) \
     X(1, 2) X(2, 2) X(3, 2) X(4, 2) X(6, 2) X(8, 2) \
-    X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4)
+    X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4) X(9, 4) X(10, 4)
 
 // Fused register loops for rows of 257..512 columns (4 float4 per lane).
-#define CSK_FUSED_REG_VARIANTS(X) X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4)
+#define CSK_FUSED_REG_VARIANTS(X) \
+    X(1, 4) X(2, 4) X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4) X(9, 4) X(10, 4)
 
 const void* fused_reg_kernel(int rpw, int cpl) {
 #define CSK_PICK(RPWv, CPLv) \
@@ -756,7 +758,7 @@ bool reg_shape(int rows_per_cta, int n, int* rpw, int* cpl) {
     const int need_c = (n / 4 + 31) / 32;
     const int need_r = (rows_per_cta + kWarps - 1) / kWarps;
     const int cs[] = {1, 2, 4};
-    const int rs[] = {1, 2, 3, 4, 5, 6, 7, 8};
+    const int rs[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10};
     for (int c : cs) {
         if (c < need_c) continue;
         for (int r : rs) {

@@ -115,16 +115,17 @@ __device__ __forceinline__ void warp_reduce(Red<double>& c) {
 }
 
 // --------------------------------------------------- row sums of a warp
-// Sums of a warp's N rows (N = 1, 2, 4, 8; a[u] = this lane's partial of row
+// Sums of a warp's N rows (N = 1, 2, 4, 8, 16; a[u] = this lane's partial of row
 // u) by a transposed butterfly: each of the first log2(N) levels halves the
 // rows a lane carries, so the N sums cost 5 + N - 1 shuffles and adds instead
-// of 5 N, and lane l ends with the sum of row transpose_row<N>(l) (lane bits
-// 4, 3, 2 from the top).  Every level adds the same pairs as the xor
+// of 5 N, and lane l ends with the sum of row transpose_row<N>(l) (the top
+// log2(N) lane bits, bit 4 the row's highest).  Every level adds the same pairs as the xor
 // butterfly of warp_sum (16, 8, 4, 2, 1), so each sum is bit for bit the
 // warp_sum of its row.
 template <int N>
 __device__ __forceinline__ int transpose_row(int lane) {
-    return N == 8 ? ((lane >> 2) & 7) : N == 4 ? ((lane >> 3) & 3) : N == 2 ? ((lane >> 4) & 1) : 0;
+    return N == 16 ? ((lane >> 1) & 15) : N == 8 ? ((lane >> 2) & 7) : N == 4 ? ((lane >> 3) & 3)
+         : N == 2 ? ((lane >> 4) & 1) : 0;
 }
 
 // The lane of each group holding one row that reports it (lowest free bits 0).
@@ -135,7 +136,7 @@ __device__ __forceinline__ bool transpose_rep(int lane) {
 
 template <typename T, int N>
 __device__ __forceinline__ T transpose_sum(const T (&a)[N], int lane) {
-    static_assert(N == 1 || N == 2 || N == 4 || N == 8, "N = 1, 2, 4 or 8");
+    static_assert(N == 1 || N == 2 || N == 4 || N == 8 || N == 16, "N = 1, 2, 4, 8 or 16");
     T v[N];
 #pragma unroll
     for (int u = 0; u < N; ++u) v[u] = a[u];
@@ -157,8 +158,8 @@ __device__ __forceinline__ T transpose_sum(const T (&a)[N], int lane) {
 }
 
 template <int R>
-struct Pow2Rows {   // smallest of 1, 2, 4, 8 holding R rows
-    static constexpr int N = R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8;
+struct Pow2Rows {   // smallest of 1, 2, 4, 8, 16 holding R rows
+    static constexpr int N = R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : R <= 8 ? 8 : 16;
 };
 
 // CTA-wide reduction with a single barrier: warps post their partial results

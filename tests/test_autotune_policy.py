@@ -13,8 +13,8 @@ def test_candidates_large_problem_adds_small_counts():
     assert {152, 137, 128, 114, 100, 91, 76} <= set(c)
     assert {8, 16, 32, 64} <= set(c)
     assert max(c) <= 152
-    # the fewest CTAs holding 5000 rows at 8, 7, 6, 5 rows per warp (8 warps)
-    assert {79, 90, 105, 125} <= set(c)
+    # the fewest CTAs holding 5000 rows at 10, 9, 8, 7, 6, 5 rows per warp (8 warps)
+    assert {63, 70, 79, 90, 105, 125} <= set(c)
 
 
 def test_candidates_small_problem_keeps_four_rows_per_cta():

@@ -263,6 +263,25 @@ def test_stream_variant_equals_register_variant(csk, grid):
     assert np.array_equal(x2.view(np.uint32), x3.view(np.uint32))
 
 
+@pytest.mark.parametrize("grid", [25, 28])
+def test_register_loop_nine_and_ten_rows_per_warp(csk, grid):
+    """At d = 2000 with rows of 300 columns (4 float4 per lane), 25 and 28
+    CTAs put 10 and 9 rows on each warp of the register loop (the 16-row
+    transposed butterfly, lanes paired per row).  Its iterates equal the
+    streamed variant's bit for bit, and every step replays in FP64 against
+    the oracle's FP32 same-order sketch."""
+    m, n, d, seed = 40000, 300, 2000, 12
+    s = synth.gaussian_system(m, n, seed, np.float32)
+    x2, i2, k2, X = _solve(csk, s, d, seed, log=5000, xlog=5000, grid=grid, gemv_variant=2)
+    x3, i3, k3 = _solve(csk, s, d, seed, log=5000, grid=grid, gemv_variant=3)
+    assert i2["status"] == 0 and i2["rse"] <= 1e-6 and i2["grid"] == grid
+    assert i2["iters"] == i3["iters"] and np.array_equal(k2, k3)
+    assert np.array_equal(x2.view(np.uint32), x3.view(np.uint32))
+    h, sg = oracle.count_sketch_map(seed, m, d)
+    At32, bt32 = oracle.sketch_f32_same_order(s.A, s.b, h, sg, d)
+    _check_steps(At32, bt32, X, k2, i2["iters"] - 1, 2.0 ** -24)
+
+
 @pytest.mark.parametrize("pad", [0, 4])
 def test_stream_variant_unsketched_mwrk(csk, pad):
     """MWRK on A itself (Remark 1, d = 0) streams A every step: the oracle's
