@@ -347,13 +347,21 @@ __device__ __forceinline__ void gemv_loop(const IterProblem& p, int R, int cache
     int64_t k = 0;
     int status = CSK_OK;
     for (;;) {
-        // Phase A: residuals of the owned rows.  Warp w scores rows
-        // w, w + kWarps, ... (round robin), up to NR in one pass
-        // over the columns so their loads overlap.
+        // Phase A: residuals of the owned rows.  FP32: warp w scores rows
+        // w, w + kWarps, ... (round robin), up to NR in one pass over the
+        // columns so their loads overlap.  FP64: warp w scores NR
+        // consecutive rows w NR, ..., then w NR + kWarps NR, ...: this GPU
+        // issues an FP64 warp instruction at the same cost whatever its
+        // active lanes, so few warps with many rows each (one transposed
+        // butterfly and one key computation for NR rows) take fewer FP64
+        // instructions than many warps with few rows.
+        constexpr bool kContig = sizeof(T) == 8;
         Red<T> c;
         c.key = T(-1); c.alpha = T(0); c.stat = T(0); c.idx = INT_MAX;
-        for (int base = warp; base < nr; base += kWarps * NR) {
-            const int myrows = min(NR, (nr - base + kWarps - 1) / kWarps);
+        for (int base = kContig ? warp * NR : warp; base < nr; base += kWarps * NR) {
+            const int myrows = kContig ? min(NR, nr - base)
+                                       : min(NR, (nr - base + kWarps - 1) / kWarps);
+            const int rstride = kContig ? 1 : kWarps;      // between a warp's rows of one pass
             T acc[NR];
 #pragma unroll
             for (int u = 0; u < NR; ++u) acc[u] = T(0);
@@ -365,7 +373,7 @@ __device__ __forceinline__ void gemv_loop(const IterProblem& p, int R, int cache
                     for (int u = 0; u < NR; ++u)
                         if (u < myrows) {
                             const float4 a = reinterpret_cast<const float4*>(
-                                Abase + (int64_t)(base + u * kWarps) * lda)[c4];
+                                Abase + (int64_t)(base + u * rstride) * lda)[c4];
                             acc[u] = fma((T)a.x, (T)xv.x, acc[u]);
                             acc[u] = fma((T)a.y, (T)xv.y, acc[u]);
                             acc[u] = fma((T)a.z, (T)xv.z, acc[u]);
@@ -377,14 +385,14 @@ __device__ __forceinline__ void gemv_loop(const IterProblem& p, int R, int cache
                     const T xv = xs[col];
 #pragma unroll
                     for (int u = 0; u < NR; ++u)
-                        if (u < myrows) acc[u] = fma(Abase[(int64_t)(base + u * kWarps) * lda + col], xv, acc[u]);
+                        if (u < myrows) acc[u] = fma(Abase[(int64_t)(base + u * rstride) * lda + col], xv, acc[u]);
                 }
             }
             // lane l ends with row u(l)'s sum, bit for bit the warp_sum of that row
             const T sum = transpose_sum<T, NR>(acc, lane);
             const int u = transpose_row<NR>(lane);
             if (transpose_rep<NR>(lane) && u < myrows) {
-                const int q = base + u * kWarps;
+                const int q = base + u * rstride;
                 const T r = bts[q] - sum;
                 const T w = w2s[q];
                 if (!below_zero(w)) {
@@ -1054,9 +1062,16 @@ k_iterate_gemv_stream(IterProblem p, int R, int nst) {
 // Shared-memory GEMV loop: rows a warp scores in one pass, the smallest of
 // 1, 2, 4, 8 covering its share of the CTA's rows (a transposed butterfly
 // over N rows costs N + 4 adds, FP64 ones on the slow pipe).
+// Rows a warp scores in one pass: FP32 spreads a CTA's rows over all its
+// warps; FP64 packs up to kRowsPerWarp consecutive rows on each warp (see
+// the loop's Phase A).
+int gemv_rows_per_pass(int dtype, int rows_per_cta) {
+    const int rpw = dtype == CSK_F64 ? rows_per_cta : (rows_per_cta + kWarps - 1) / kWarps;
+    return rpw <= 1 ? 1 : rpw <= 2 ? 2 : rpw <= 4 ? 4 : kRowsPerWarp;
+}
+
 const void* gemv_kernel(int dtype, int rows_per_cta) {
-    const int rpw = (rows_per_cta + kWarps - 1) / kWarps;
-    const int nr = rpw <= 1 ? 1 : rpw <= 2 ? 2 : rpw <= 4 ? 4 : kRowsPerWarp;
+    const int nr = gemv_rows_per_pass(dtype, rows_per_cta);
     const bool f64 = dtype == CSK_F64;
     switch (nr) {
         case 1: return f64 ? (const void*)k_iterate_gemv<double, 1> : (const void*)k_iterate_gemv<float, 1>;
@@ -1081,8 +1096,7 @@ const void* stream_kernel_t(int dtype, int cpl) {
 // Fused kernel of the shared-memory GEMV loop; vec: 16-byte loads of A in
 // the sketch (A 16-byte aligned, n and lda multiples of the vector).
 const void* fused_gemv_kernel(int dtype, int rows_per_cta, bool vec) {
-    const int rpw = (rows_per_cta + kWarps - 1) / kWarps;
-    const int nr = rpw <= 1 ? 1 : rpw <= 2 ? 2 : rpw <= 4 ? 4 : kRowsPerWarp;
+    const int nr = gemv_rows_per_pass(dtype, rows_per_cta);
 #define CSK_F(T, NR) (vec ? (const void*)k_fused_gemv<T, NR, (sizeof(T) == 8 ? 2 : 4), (sizeof(T) == 8 ? 2 : 4)> \
                          : (const void*)k_fused_gemv<T, NR, 1, 4>)
     if (dtype == CSK_F64)
