@@ -33,6 +33,7 @@ namespace csk {
 
 template <typename T, int V> struct VecOf;
 template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<float, 2> { using type = float2; };
 template <> struct VecOf<float, 1> { using type = float; };
 template <> struct VecOf<double, 2> { using type = double2; };
 template <> struct VecOf<double, 1> { using type = double; };

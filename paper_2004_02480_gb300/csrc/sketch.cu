@@ -636,7 +636,9 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     const void* fn = nullptr;
     if (dtype == CSK_F32) {
         const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
-        fn = vec ? (const void*)k_segsum<float, 4, 1, 4> : (const void*)k_segsum<float, 1, 4, 4>;
+        const bool vec2 = (a % 8 == 0) && (lda % 2 == 0) && (n % 2 == 0);   // 8-byte loads
+        fn = vec ? (const void*)k_segsum<float, 4, 1, 4>
+           : vec2 ? (const void*)k_segsum<float, 2, 2, 4> : (const void*)k_segsum<float, 1, 4, 4>;
     } else {
         const bool vec = (a % 16 == 0) && (lda % 2 == 0) && (n % 2 == 0);
         if (vec) {
@@ -745,8 +747,14 @@ cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, con
     if (cap_env > 0) cap = cap_env;
     const size_t smem = (size_t)2 * cap * sizeof(int32_t);
     const int n4 = n / 4;
+    // 8-byte loads when rows are 8-byte aligned but not 16 (n even, n % 4 = 2)
+    const bool vec2 = !vec && (reinterpret_cast<uintptr_t>(A) % 8 == 0) && (lda % 2 == 0) &&
+                      (n % 2 == 0);
+    const int n2 = n / 2;
     const void* fn = vec ? (n4 <= 32 ? (const void*)k_sketch_own<4, 1>
                             : n4 <= 64 ? (const void*)k_sketch_own<4, 2> : (const void*)k_sketch_own<4, 4>)
+                   : vec2 ? (n2 <= 32 ? (const void*)k_sketch_own<2, 1>
+                             : n2 <= 64 ? (const void*)k_sketch_own<2, 2> : (const void*)k_sketch_own<2, 4>)
                          : (n <= 32 ? (const void*)k_sketch_own<1, 1> : (const void*)k_sketch_own<1, 4>);
     e = ensure_smem_attr(fn, smem);
     if (e != cudaSuccess) return e;
