@@ -14,6 +14,10 @@
 //                 and ||At_j||^2 in FP64: a warp per column chunk (128
 //                 columns in FP32; up to 256, sized to the row, in FP64),
 //                 16-byte loads, 4 (narrow FP64 rows: 8) rows in flight
+//   k_segsum_warp the same sums for FP32 with at most 128 rows per bucket on
+//                 average and enough buckets to occupy the warps: a warp per
+//                 bucket over up to 512 columns at once, ordered by
+//                 shuffles, no CTA barrier; bt as well for one right-hand side
 //   k_segsum_b1   bt likewise, FP64 with one right-hand side, a warp per 8
 //                 buckets
 //   k_segsum_b    Bt likewise otherwise, a warp per bucket
@@ -501,6 +505,121 @@ k_segsum_b(const T* __restrict__ B, int64_t ldb, int nrhs, const int32_t* __rest
     }
 }
 
+// ------------------------------------------ warp-per-bucket segmented sum
+// FP32 sketches whose buckets hold at most kWarpMean rows on average: each
+// warp claims a bucket of its own and runs it through without a CTA barrier,
+// so one warp's claim, ordering and final sums overlap the other warps' row
+// loads (with 20 to 50 rows per bucket those fixed steps are a large part of
+// a bucket), and a lane keeps 32 values in flight across up to 512 columns
+// (twice the CTA kernel's 16 over 128) at 60 to 68 registers.  A bucket of
+// at most kWarpCap rows is ordered in registers (lane l holds rows l and
+// l + 32 of the scatter's order and counts, by shuffles, how many of the
+// bucket's rows are smaller: its rank); the ordered rows go to a
+// warp-private list in shared memory and to perm.  A larger bucket is
+// ranked against perm_tmp in global memory and read back from perm.  Then
+// the warp sums every column chunk of the bucket in ascending row order (the
+// same additions as k_segsum) and, with one right-hand side, bt_j as
+// k_segsum_b does: the signed values of the rows added in ascending order,
+// their loads issued before the column pass and consumed after it.
+constexpr int kWarpCap = 64;
+constexpr int kWarpMean = 128;
+constexpr int kWarpThreads = 128;
+
+template <int V, int CPL, int U>
+__global__ void __launch_bounds__(kWarpThreads, CPL >= 4 ? 7 : 8)
+k_segsum_warp(const float* __restrict__ A, int64_t lda, int n, const int32_t* __restrict__ perm_tmp,
+              int32_t* __restrict__ perm, const int32_t* __restrict__ off, int d, uint64_t seed,
+              float* __restrict__ At, double* __restrict__ N2, int32_t* __restrict__ next,
+              const float* __restrict__ B, int64_t ldb, float* __restrict__ Bt) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ __align__(16) int32_t list[kWarpThreads / 32][kWarpCap];
+    constexpr int CW = 32 * V * CPL;                 // columns per chunk
+    const int lane = lane_id();
+    int32_t* my = list[threadIdx.x >> 5];
+    for (;;) {
+        int32_t j = 0;
+        if (lane == 0) j = atomicAdd(next, 1);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= d) break;
+        const int32_t p0 = off[j], cnt = off[j + 1] - p0;
+        const bool small = cnt <= kWarpCap;
+        const int32_t* rows = my;
+        int32_t q0 = 0;
+        if (small) {
+            const int32_t v0 = lane < cnt ? perm_tmp[p0 + lane] : INT_MAX;
+            const int32_t v1 = lane + 32 < cnt ? perm_tmp[p0 + 32 + lane] : INT_MAX;
+            int r0 = 0, r1 = 0;
+            const int c32 = cnt < 32 ? cnt : 32;
+            for (int q = 0; q < c32; ++q) {
+                const int32_t u = __shfl_sync(0xffffffffu, v0, q);
+                r0 += u < v0;
+                r1 += u < v1;
+            }
+            for (int q = 32; q < cnt; ++q) {
+                const int32_t u = __shfl_sync(0xffffffffu, v1, q - 32);
+                r0 += u < v0;
+                r1 += u < v1;
+            }
+            if (lane < cnt) {
+                my[r0] = v0;
+                perm[p0 + r0] = v0;
+            }
+            if (lane + 32 < cnt) {
+                my[r1] = v1;
+                perm[p0 + r1] = v1;
+            }
+        } else {
+            for (int t = lane; t < cnt; t += 32) {
+                const int32_t v = perm_tmp[p0 + t];
+                int rank = 0;
+                for (int q = 0; q < cnt; ++q) rank += perm_tmp[p0 + q] < v;
+                perm[p0 + rank] = v;
+            }
+            rows = perm;
+            q0 = p0;
+        }
+        __syncwarp();
+        float b0 = 0.f, b1 = 0.f;
+        if (Bt && small) {
+            if (lane < cnt) {
+                const int32_t r = my[lane];
+                b0 = B[(int64_t)r * ldb];
+                if (row_negative(row_hash(seed, (uint64_t)r))) b0 = -b0;
+            }
+            if (lane + 32 < cnt) {
+                const int32_t r = my[lane + 32];
+                b1 = B[(int64_t)r * ldb];
+                if (row_negative(row_hash(seed, (uint64_t)r))) b1 = -b1;
+            }
+        }
+        double sq = 0.0;
+        for (int c0 = 0; c0 < n; c0 += CW)
+            sq += seg_chunk<float, V, CPL, U>(A, lda, n, c0, rows, q0, q0 + cnt, seed, At + (int64_t)j * n);
+        sq = warp_sum(sq);
+        if (lane == 0 && N2) N2[j] = sq;
+        if (Bt) {
+            float acc = 0.f;
+            if (small) {
+                const int c32 = cnt < 32 ? cnt : 32;
+                for (int q = 0; q < c32; ++q) acc += __shfl_sync(0xffffffffu, b0, q);
+                for (int q = 32; q < cnt; ++q) acc += __shfl_sync(0xffffffffu, b1, q - 32);
+            } else {
+                for (int32_t pb = 0; pb < cnt; pb += 32) {
+                    const bool valid = pb + lane < cnt;
+                    const int32_t r = valid ? rows[q0 + pb + lane] : 0;
+                    float v = valid ? B[(int64_t)r * ldb] : 0.f;
+                    if (row_negative(row_hash(seed, (uint64_t)r))) v = -v;
+                    const int c = min(32, cnt - pb);
+                    for (int q = 0; q < c; ++q) acc += __shfl_sync(0xffffffffu, v, q);
+                }
+            }
+            if (lane == 0) Bt[j] = acc;
+        }
+        __syncwarp();   // the list is rewritten for the next bucket
+    }
+}
+
 // --------------------------------------------- bucket-owner sketch (FP32)
 // FP32 sketches whose buckets are small (at most kOwnMaxMean rows on
 // average, d <= 65535) and whose A is at most kOwnMaxElems elements skip the
@@ -511,6 +630,7 @@ constexpr int kOwnThreads = 512;
 constexpr int kOwnMaxMean = 128;          // mean rows per bucket of this path
 constexpr int64_t kOwnMaxElems = 32ll << 20;   // elements of A of this path (by default)
 constexpr int kOwnMaxCap = 16384;         // rows a CTA lists in shared memory at most
+constexpr int64_t kOwnWarpElems = 4ll << 20;   // elements of A from which the warp-per-bucket sum may win
 
 __global__ void k_hash16(int64_t m, uint32_t d, uint64_t seed, uint16_t* __restrict__ h) {
     hash16_range(m, d, seed, h, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
@@ -621,6 +741,84 @@ cudaError_t launch_bucket_group(int64_t m, int64_t d, uint64_t seed, const SortS
     return e;
 }
 
+namespace {
+int sketch_path_override();
+
+// Bt for the right-hand sides after the segmented sum of A has written perm.
+cudaError_t launch_segsum_rhs(int dtype, const void* B, int64_t ldb, int nrhs, const SortScratch& s,
+                              int d, uint64_t seed, void* Bt, const DevInfo& di, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (B && nrhs == 1 && dtype == CSK_F64) {
+        int64_t bblocks = ((int64_t)d + kBWarps * kBGroup - 1) / (kBWarps * kBGroup);
+        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
+        e = launch_dep(k_segsum_b1<double>, (int)bblocks, 32 * kBWarps, st, (const double*)B, ldb,
+                       s.perm, s.off, d, seed, (double*)Bt);
+        note_launches(1);
+    } else if (B && nrhs > 0) {
+        int64_t bblocks = ((int64_t)d + 7) / 8;
+        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
+        if (dtype == CSK_F32)
+            e = launch_dep(k_segsum_b<float>, (int)bblocks, 256, st, (const float*)B, ldb, nrhs,
+                           s.perm, s.off, d, seed, (float*)Bt);
+        else
+            e = launch_dep(k_segsum_b<double>, (int)bblocks, 256, st, (const double*)B, ldb, nrhs,
+                           s.perm, s.off, d, seed, (double*)Bt);
+        note_launches(1);
+    }
+    return e;
+}
+
+// FP32: the warp-per-bucket kernel for the row layout.  32 values a lane in
+// flight (8 16-byte, 16 8-byte or 32 4-byte loads), over up to 512 columns
+// at once.
+using WarpSegsumFn = decltype(&k_segsum_warp<4, 1, 8>);
+WarpSegsumFn pick_segsum_warp(const float* A, int64_t lda, int n) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A);
+    const bool vec = (a % 16 == 0) && (lda % 4 == 0) && (n % 4 == 0);
+    const bool vec2 = (a % 8 == 0) && (lda % 2 == 0) && (n % 2 == 0);   // 8-byte loads
+    if (vec) return n <= 128 ? k_segsum_warp<4, 1, 8> : n <= 256 ? k_segsum_warp<4, 2, 4> : k_segsum_warp<4, 4, 2>;
+    if (vec2) return n <= 128 ? k_segsum_warp<2, 2, 8> : n <= 256 ? k_segsum_warp<2, 4, 4> : k_segsum_warp<2, 8, 2>;
+    return k_segsum_warp<1, 4, 8>;
+}
+
+// Whether the warp-per-bucket kernel takes an FP32 sketch: buckets of at most
+// kWarpMean rows on average, and at least half as many buckets as resident
+// warps.  Measured on GB300 (whole sketch, one right-hand side): ahead of the
+// CTA per bucket from 100000 x 100 to 1e6 x 1000 and up to 120 rows per
+// bucket (300000 x 50, d = 2500), behind it with 1500 buckets for ~4000
+// warps (30000 x 1000).  *fn and *per_sm return the kernel and its residency.
+cudaError_t warp_segsum_fits(const float* A, int64_t lda, int64_t m, int n, int64_t d,
+                             const DevInfo& di, WarpSegsumFn* fn, int* per_sm, bool* fits) {
+    *fn = pick_segsum_warp(A, lda, n);
+    *per_sm = 0;
+    const cudaError_t e = cached_occupancy((const void*)*fn, kWarpThreads, 0, per_sm);
+    if (e != cudaSuccess) return e;
+    const int64_t warps = (int64_t)*per_sm * di.sms * (kWarpThreads / 32);
+    *fits = m <= (int64_t)kWarpMean * d && 2 * d >= warps;
+    return cudaSuccess;
+}
+
+// k_segsum_warp on per_sm resident CTAs a SM (their warps claim the
+// buckets; at most one warp per bucket); it also sums bt for one right-hand
+// side, k_segsum_b the others.
+cudaError_t launch_segsum_warp(WarpSegsumFn fn, int per_sm, const float* A, int64_t lda, int n,
+                               const float* B, int64_t ldb, int nrhs, const SortScratch& s, int d,
+                               uint64_t seed, float* At, float* Bt, double* N2, const DevInfo& di,
+                               cudaStream_t st) {
+    const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * di.sms;
+    const int64_t need = ((int64_t)d + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
+    const int blocks = (int)(resident < need ? resident : need);
+    const bool fold_b = B && nrhs == 1;
+    cudaError_t e = launch_dep(fn, blocks, kWarpThreads, st, A, lda, n, s.perm_tmp, s.perm, s.off, d,
+                               seed, At, N2, s.cnt + d, fold_b ? B : nullptr, ldb,
+                               fold_b ? Bt : nullptr);
+    note_launches(1);
+    if (e == cudaSuccess && !fold_b)
+        e = launch_segsum_rhs(CSK_F32, B, ldb, nrhs, s, d, seed, Bt, di, st);
+    return e;
+}
+}  // namespace
+
 cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
                           int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
                           void* At, void* Bt, double* N2, cudaStream_t st) {
@@ -632,6 +830,19 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     // lanes hold, so an FP64 row of up to 256 columns is one chunk sized to
     // it (no chunk half made of zeros), and a row of at most 64 columns keeps
     // 8 rows in flight instead of 4 (a warp moves few bytes per row).
+    // FP32: a warp per bucket where warp_segsum_fits says so
+    const int o = sketch_path_override();
+    if (dtype == CSK_F32 && o != 4) {
+        WarpSegsumFn wf;
+        int per_sm = 0;
+        bool fits = false;
+        cudaError_t e = warp_segsum_fits(static_cast<const float*>(A), lda, m, n, d, di, &wf, &per_sm, &fits);
+        if (e != cudaSuccess) return e;
+        if (o == 3 || fits)
+            return launch_segsum_warp(wf, per_sm, static_cast<const float*>(A), lda, n,
+                                      static_cast<const float*>(B), ldb, nrhs, s, d, seed,
+                                      static_cast<float*>(At), static_cast<float*>(Bt), N2, di, st);
+    }
     int cw = 128;
     const void* fn = nullptr;
     if (dtype == CSK_F32) {
@@ -670,31 +881,17 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
                        bs, st, (const double*)A, lda, n, m, s.perm_tmp, s.perm, s.off, d, seed,
                        (double*)At, N2, s.cnt + d);
     note_launches(1);
-    if (e == cudaSuccess && B && nrhs == 1 && dtype == CSK_F64) {
-        int64_t bblocks = ((int64_t)d + kBWarps * kBGroup - 1) / (kBWarps * kBGroup);
-        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
-        e = launch_dep(k_segsum_b1<double>, (int)bblocks, 32 * kBWarps, st, (const double*)B, ldb,
-                       s.perm, s.off, d, seed, (double*)Bt);
-        note_launches(1);
-    } else if (e == cudaSuccess && B && nrhs > 0) {
-        int64_t bblocks = ((int64_t)d + 7) / 8;
-        if (bblocks > (int64_t)di.sms * 32) bblocks = (int64_t)di.sms * 32;
-        if (dtype == CSK_F32)
-            e = launch_dep(k_segsum_b<float>, (int)bblocks, 256, st, (const float*)B, ldb, nrhs,
-                           s.perm, s.off, d, seed, (float*)Bt);
-        else
-            e = launch_dep(k_segsum_b<double>, (int)bblocks, 256, st, (const double*)B, ldb, nrhs,
-                           s.perm, s.off, d, seed, (double*)Bt);
-        note_launches(1);
-    }
+    if (e == cudaSuccess) e = launch_segsum_rhs(dtype, B, ldb, nrhs, s, d, seed, Bt, di, st);
     return e;
 }
 
 namespace {
 // Test and measurement hooks read once from the environment: CSK_SKETCH_PATH
 // = "sort" or "own" forces the counting-sort or the bucket-owner FP32 path
-// (where the owner path applies); CSK_SKETCH_OWN_CAP caps a CTA's row list
-// (exercises the sub-range and large-bucket code of the owner path).
+// (where the owner path applies), "warp" or "cta" the counting sort with the
+// warp-per-bucket or the CTA-per-bucket segmented sum (FP32; FP64 always
+// takes the CTA one); CSK_SKETCH_OWN_CAP caps a CTA's row list (exercises
+// the sub-range and large-bucket code of the owner path).
 int env_int(const char* name, int dflt) {
     const char* v = getenv(name);
     return (v && *v) ? atoi(v) : dflt;
@@ -705,20 +902,37 @@ int sketch_path_override() {
         if (!v) return 0;
         if (!strcmp(v, "sort")) return 1;
         if (!strcmp(v, "own")) return 2;
+        if (!strcmp(v, "warp")) return 3;
+        if (!strcmp(v, "cta")) return 4;
         return 0;
     }();
     return p;
 }
 
-bool use_owner_path(int dtype, int64_t m, int64_t n, int64_t d) {
+bool use_owner_path(int dtype, const void* A, int64_t lda, int64_t m, int64_t n, int64_t d,
+                    int nrhs) {
     if (dtype != CSK_F32 || d > 65535 || m > (int64_t)INT_MAX / 2) return false;
     const int o = sketch_path_override();
-    if (o == 1) return false;
     if (o == 2) return true;
-    // measured on GB300: ahead of the counting sort up to ~25M elements of A
-    // (fixed costs of the sort chain dominate there), behind it at
-    // 100000 x 500 with one right-hand side and above
-    return m <= (int64_t)kOwnMaxMean * d && m * (int64_t)n <= kOwnMaxElems;
+    if (o != 0) return false;
+    // measured on GB300: ahead of the counting sort with the CTA-per-bucket
+    // sum up to ~25M elements of A (fixed costs of the sort chain dominate
+    // there), behind it at 100000 x 500 with one right-hand side and above
+    if (!(m <= (int64_t)kOwnMaxMean * d && m * (int64_t)n <= kOwnMaxElems)) return false;
+    // with at most one right-hand side and from kOwnWarpElems elements of A,
+    // the sort chain with the warp-per-bucket sum is ahead where it applies
+    // (100000 x 100, d = 5000: 31 against 47 us; 300000 x 100, d = 10000: 55
+    // against 104; 20000 x 100, d = 1000: even)
+    if (nrhs > 1 || m * (int64_t)n < kOwnWarpElems) return true;
+    DevInfo di;
+    if (dev_info(&di) != 0) return true;
+    WarpSegsumFn wf;
+    int per_sm = 0;
+    bool fits = false;
+    if (warp_segsum_fits(static_cast<const float*>(A), lda, m, (int)n, d, di, &wf, &per_sm, &fits) !=
+        cudaSuccess)
+        return true;
+    return !fits;
 }
 
 cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, const float* B,
@@ -781,7 +995,7 @@ cudaError_t launch_sketch_own(const float* A, int64_t lda, int64_t m, int n, con
 cudaError_t launch_sketch(int dtype, const void* A, int64_t lda, int64_t m, int n, const void* B,
                           int64_t ldb, int nrhs, const SortScratch& s, int d, uint64_t seed,
                           void* At, void* Bt, double* N2, cudaStream_t st) {
-    if (use_owner_path(dtype, m, n, d))
+    if (use_owner_path(dtype, A, lda, m, n, d, nrhs))
         return launch_sketch_own(static_cast<const float*>(A), lda, m, n,
                                  nrhs > 0 ? static_cast<const float*>(B) : nullptr, ldb, nrhs, s, d,
                                  seed, static_cast<float*>(At), static_cast<float*>(Bt), N2, st);

@@ -19,7 +19,8 @@ from paper_2004_02480_gb300 import csk  # noqa: E402
 
 CASES = [(100000, 500, 5000, 1), (20000, 130, 700, 3), (5000, 64, 300, 64), (3000, 50, 20, 1),
          (7, 3, 3, 1), (1, 1, 1, 1), (2000, 33, 5000, 1), (30000, 1000, 1500, 2), (4000, 8, 40, 0),
-         (60000, 12, 600, 1), (8000, 126, 900, 1), (40000, 254, 3000, 2)]
+         (60000, 12, 600, 1), (8000, 126, 900, 1), (40000, 254, 3000, 2), (6000, 514, 200, 1),
+         (5000, 301, 250, 1), (20000, 260, 400, 1)]
 
 
 def main():

@@ -155,16 +155,20 @@ def test_sketch_full_size_precision_form_sampled(csk):
         assert np.array_equal(Atg[j], Atj[0])
 
 
-@pytest.mark.parametrize("env", [{"CSK_SKETCH_PATH": "sort"}, {"CSK_SKETCH_PATH": "own"},
+@pytest.mark.parametrize("env", [{"CSK_SKETCH_PATH": "sort"}, {"CSK_SKETCH_PATH": "cta"},
+                                 {"CSK_SKETCH_PATH": "warp"}, {"CSK_SKETCH_PATH": "own"},
                                  {"CSK_SKETCH_PATH": "own", "CSK_SKETCH_OWN_CAP": "256"},
                                  {"CSK_SKETCH_PATH": "own", "CSK_SKETCH_OWN_CAP": "16"}])
 def test_sketch_paths_bit_exact(csk, env):
-    """The counting-sort path and the bucket-owner FP32 path (forced for
-    every shape, including buckets of ~150 rows), the latter also with a
-    per-CTA row list of 256 and of 16 rows -- so its sub-range rescans and
-    its large-bucket ordering by ballot compaction run -- give the oracle's
-    offsets, permutation, At and Bt bit for bit (child process: the path is
-    read from the environment once)."""
+    """The counting-sort path (with the segmented sum the library picks, and
+    forced to the CTA-per-bucket or the warp-per-bucket kernel for every
+    shape: buckets of 0 to ~150 rows, so the warp kernel's register
+    ordering of up to 32 and of 33..64 rows and its global ordering of
+    larger buckets all run) and the bucket-owner FP32 path (forced for every
+    shape), the latter also with a per-CTA row list of 256 and of 16 rows --
+    so its sub-range rescans and its large-bucket ordering by ballot
+    compaction run -- give the oracle's offsets, permutation, At and Bt bit
+    for bit (child process: the path is read from the environment once)."""
     import os
     import subprocess
     import sys
