@@ -225,6 +225,14 @@ int csk_exchange_floor(int32_t grid, int64_t rounds, void *ws, size_t ws_bytes, 
  * ws          scratch of csk_sketch_workspace_size(m, d) bytes.
  * Limits: 1 <= m, n, d <= 2^31 - 1; m * max(n, nrhs) elements addressable.
  * d >= m is accepted (rows of At may then be zero).
+ * The library picks one of three ways to form the sums, all with the same
+ * additions in the same order and so the same bits: a counting sort of the
+ * rows by bucket followed by a segmented sum with a warp per bucket (FP32,
+ * up to 128 rows per bucket on average) or a CTA per bucket, or, for FP32
+ * problems of at most 32M elements, a pass in which each CTA owns a range
+ * of buckets and orders their rows itself.  The environment variable
+ * CSK_SKETCH_PATH = sort | own | warp | cta, read once per process, forces
+ * a way where it applies (a test and measurement aid).
  * -------------------------------------------------------------------- */
 size_t csk_sketch_workspace_size(int64_t m, int64_t d);
 
