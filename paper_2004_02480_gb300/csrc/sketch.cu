@@ -825,12 +825,9 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
     DevInfo di;
     if (dev_info(&di) != 0) return cudaErrorUnknown;
     const uintptr_t a = reinterpret_cast<uintptr_t>(A);
-    // warps per bucket: one per column chunk, at most 4.  FP32: 128-column
-    // chunks.  FP64 adds occupy the slow pipe at the same cost whatever the
-    // lanes hold, so an FP64 row of up to 256 columns is one chunk sized to
-    // it (no chunk half made of zeros), and a row of at most 64 columns keeps
-    // 8 rows in flight instead of 4 (a warp moves few bytes per row).
-    // FP32: a warp per bucket where warp_segsum_fits says so
+    // FP32: a warp per bucket where warp_segsum_fits says so.  Forced, it
+    // still needs buckets of at most kWarpMean rows on average: a bucket
+    // above kWarpCap rows is ranked in O(rows^2 / 32) steps per warp.
     const int o = sketch_path_override();
     if (dtype == CSK_F32 && o != 4) {
         WarpSegsumFn wf;
@@ -838,11 +835,16 @@ cudaError_t launch_segsum(int dtype, const void* A, int64_t lda, int64_t m, int 
         bool fits = false;
         cudaError_t e = warp_segsum_fits(static_cast<const float*>(A), lda, m, n, d, di, &wf, &per_sm, &fits);
         if (e != cudaSuccess) return e;
-        if (o == 3 || fits)
+        if (o == 3 ? m <= (int64_t)kWarpMean * d : fits)
             return launch_segsum_warp(wf, per_sm, static_cast<const float*>(A), lda, n,
                                       static_cast<const float*>(B), ldb, nrhs, s, d, seed,
                                       static_cast<float*>(At), static_cast<float*>(Bt), N2, di, st);
     }
+    // warps per bucket: one per column chunk, at most 4.  FP32: 128-column
+    // chunks.  FP64 adds occupy the slow pipe at the same cost whatever the
+    // lanes hold, so an FP64 row of up to 256 columns is one chunk sized to
+    // it (no chunk half made of zeros), and a row of at most 64 columns keeps
+    // 8 rows in flight instead of 4 (a warp moves few bytes per row).
     int cw = 128;
     const void* fn = nullptr;
     if (dtype == CSK_F32) {
@@ -889,9 +891,10 @@ namespace {
 // Test and measurement hooks read once from the environment: CSK_SKETCH_PATH
 // = "sort" or "own" forces the counting-sort or the bucket-owner FP32 path
 // (where the owner path applies), "warp" or "cta" the counting sort with the
-// warp-per-bucket or the CTA-per-bucket segmented sum (FP32; FP64 always
-// takes the CTA one); CSK_SKETCH_OWN_CAP caps a CTA's row list (exercises
-// the sub-range and large-bucket code of the owner path).
+// warp-per-bucket (where buckets hold at most kWarpMean rows on average) or
+// the CTA-per-bucket segmented sum (FP32; FP64 always takes the CTA one);
+// CSK_SKETCH_OWN_CAP caps a CTA's row list (exercises the sub-range and
+// large-bucket code of the owner path).
 int env_int(const char* name, int dflt) {
     const char* v = getenv(name);
     return (v && *v) ? atoi(v) : dflt;

@@ -161,8 +161,9 @@ def test_sketch_full_size_precision_form_sampled(csk):
                                  {"CSK_SKETCH_PATH": "own", "CSK_SKETCH_OWN_CAP": "16"}])
 def test_sketch_paths_bit_exact(csk, env):
     """The counting-sort path (with the segmented sum the library picks, and
-    forced to the CTA-per-bucket or the warp-per-bucket kernel for every
-    shape: buckets of 0 to ~150 rows, so the warp kernel's register
+    forced to the CTA-per-bucket kernel for every shape, or to the
+    warp-per-bucket kernel wherever buckets hold at most 128 rows on
+    average: buckets of 0 to ~130 rows, so the warp kernel's register
     ordering of up to 32 and of 33..64 rows and its global ordering of
     larger buckets all run) and the bucket-owner FP32 path (forced for every
     shape), the latter also with a per-CTA row list of 256 and of 16 rows --
