@@ -1,5 +1,5 @@
 """Run by tests/test_gpu_sketch.py in a child process whose environment
-forces a sketch path (CSK_SKETCH_PATH = sort | own) and, for the
+forces a sketch path (CSK_SKETCH_PATH = sort | cta | warp | own) and, for the
 bucket-owner path, a small per-CTA row list (CSK_SKETCH_OWN_CAP), which
 drives its sub-range and large-bucket code.  Every case must match the
 oracle: offsets and permutation bit for bit, At and Bt bit for bit against
