@@ -730,10 +730,10 @@ def main():
             torch.cuda.synchronize()
             fts.append(f0.elapsed_time(f1))
         floor_us = 1e3 * float(np.median(fts[1:])) / 2000
-    north = None
+    targets = None
     if world == 1 and not args.no_extras:
-        north = {"batched": batched_measure(torch, csk, dev, 3, 1),
-                 "precision_sketch_gram": sketch_gram_measure(torch, csk, dev)}
+        targets = {"batched": batched_measure(torch, csk, dev, 3, 1),
+                   "precision_sketch_gram": sketch_gram_measure(torch, csk, dev)}
 
     from paper_2004_02480_gb300 import replicas
     job = replicas.aggregate(ms * 1e-3, K, launches, ok, device=dev)
@@ -818,7 +818,7 @@ def main():
                        "csk_ms": ms / K, "csk_speedup_over_mwrk": mwrk["ms"] / (ms / K),
                        "note": "MWRK (d = 0, Remark 1) on the same A, b on the GPU, median of 3 "
                                "solves; not part of the timed steps"},
-        "north_star": north,
+        "targets": targets,
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
