@@ -54,7 +54,7 @@ typedef enum {
     CSK_ETIMEOUT = -3,     /* an inter-CTA wait exceeded its poll limit     */
     CSK_ENUMERIC = -4,     /* NaN/Inf residual, or At has no non-zero row   */
     CSK_ECUDA = -5,        /* a CUDA runtime call failed                    */
-    CSK_EUNSUPPORTED = -6  /* valid request this build does not support     */
+    CSK_EUNSUPPORTED = -6  /* valid request this library does not support   */
 } csk_status;
 
 typedef enum { CSK_F32 = 0, CSK_F64 = 1 } csk_dtype;

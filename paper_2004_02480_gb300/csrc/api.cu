@@ -394,7 +394,7 @@ const char* csk_strerror(int status) {
         case CSK_ETIMEOUT: return "CSK_ETIMEOUT: inter-CTA wait exceeded its poll limit";
         case CSK_ENUMERIC: return "CSK_ENUMERIC: NaN/Inf residual or no non-zero row";
         case CSK_ECUDA: return "CSK_ECUDA: CUDA runtime error";
-        case CSK_EUNSUPPORTED: return "CSK_EUNSUPPORTED: not supported by this build";
+        case CSK_EUNSUPPORTED: return "CSK_EUNSUPPORTED: not supported by this library";
         default: return "unknown csk status";
     }
 }
